@@ -1,0 +1,179 @@
+/*
+ * libtucker: sparse Tucker decomposition by HOOI with QR column pivoting on one GPU
+ * (sm_103a).  Method: Jiang, Zhang, Lin, Xing, Zhang, "Sparse Tucker Tensor
+ * Decomposition on a Hybrid FPGA-CPU Platform", arXiv 2010.10638.
+ *
+ * C ABI.  No C++ or framework types cross it: plain pointers, sizes and a CUDA
+ * stream passed as `void *` (a cudaStream_t; NULL is the legacy default stream).
+ *
+ * General conventions
+ *   - Every call is asynchronous on `stream` unless stated otherwise.
+ *   - A return value other than TUCKER_OK means that no output was written.
+ *   - Errors that only the device can see (a coordinate out of range, a non-finite
+ *     value, a bounded wait that gave up) are latched in a per-context device word
+ *     and reported by the next call that synchronises (tucker_init,
+ *     hooi_iter with a host fit pointer, tucker_sync_status).
+ *   - No exception or longjmp crosses the ABI.  Calls on one context are not
+ *     thread-safe; distinct contexts are independent.
+ *   - Modes are 0-based.  Order N is 2..8.  Indices are 0-based uint32.
+ *   - Matrices are row-major.  Factor U_m is I_m x R_m.  The mode-n TTMc output
+ *     Y_(n) is I_n x P_n with P_n = prod_{m != n} R_m; its columns follow the
+ *     Kronecker layout of Algorithm 4: the remaining modes in ascending order, the
+ *     last one varying fastest.  The core tensor G is C-order [R_1]...[R_N].
+ *   - The caller owns every pointer it passes.  A context owns its internal device
+ *     copies (sorted nonzeros, factors, workspaces) until tucker_free.
+ */
+#ifndef TUCKER_H
+#define TUCKER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define TUCKER_API __attribute__((visibility("default")))
+#else
+#define TUCKER_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tucker_ctx tucker_ctx;
+
+typedef enum {
+  TUCKER_OK = 0,
+  TUCKER_EINVAL = 1,   /* bad argument: null pointer, size, order, coordinate, value */
+  TUCKER_ERANK = 2,    /* rank outside 1 <= R_n <= I_n (and R_n <= P_n for direct QRP) */
+  TUCKER_ENOMEM = 3,   /* a device or host allocation failed; the context stays freeable */
+  TUCKER_ECUDA = 4,    /* a CUDA runtime call failed (message in tucker_last_error) */
+  TUCKER_ETIMEOUT = 5, /* a bounded device-side wait gave up */
+  TUCKER_ESTATE = 6    /* call out of order (e.g. core tensor before any sweep) */
+} tucker_status;
+
+/* Flags for tucker_init. */
+#define TUCKER_F_BF16_FACTORS 0x1u /* TTMc reads BF16 copies of the factors (FP32 accumulation) */
+#define TUCKER_F_QRP_DIRECT 0x2u   /* fat Y_(n) (P_n > I_n): QRP on Y_(n) itself, not on Y Y^T */
+#define TUCKER_F_HOST_INPUT 0x4u   /* coords, vals and U0 given to tucker_init are host pointers */
+#define TUCKER_F_FIT_DEVICE 0x8u   /* hooi_iter writes the fit through a device pointer, no sync */
+
+/*
+ * tucker_init — load a sparse tensor and prepare it for HOOI (Algorithm 2 input:
+ * the sparse tensor X and the ranks R_1..R_N; COO storage, Section III-A).
+ *
+ *   out     receives the new context (set to NULL on failure)
+ *   order   N, 2..8
+ *   dims    host array [N]: I_1..I_N, each 1..2^31-1
+ *   nnz     number of listed entries (>= 0; may be 0)
+ *   coords  [N][nnz] uint32, structure-of-arrays (coords[m*nnz + z] is i_m of entry
+ *           z), 0-based; device memory, or host with TUCKER_F_HOST_INPUT
+ *   vals    [nnz] float; device, or host with TUCKER_F_HOST_INPUT
+ *   ranks   host array [N]: R_1..R_N, 1 <= R_n <= I_n, prod R_n <= 2^20
+ *   U0      initial factors, the N matrices [I_m x R_m] (FP64, row-major) one after
+ *           another; device, or host with TUCKER_F_HOST_INPUT.  U0 for mode 1 is
+ *           never read (mode 1 is updated first).  NULL draws each U_m from a seeded
+ *           N(0,1) and orthonormalises it by Householder QR on the device.
+ *   seed    seed for the NULL-U0 case
+ *   flags   TUCKER_F_* bits
+ *
+ * Entries naming the same coordinate are summed (FP64) into one nonzero; ||X||^2
+ * is taken over the summed values.  For every mode the context builds a copy of the
+ * nonzeros sorted by that mode's index (stable), the offsets of each non-empty
+ * slice, and a table of work units of near-equal nonzero count.
+ * Synchronises `stream` once (the coalesced count sizes the copies) and returns
+ * TUCKER_EINVAL for a coordinate >= I_m or a non-finite value.
+ */
+TUCKER_API tucker_status tucker_init(tucker_ctx **out, int order, const int64_t *dims, int64_t nnz,
+                          const uint32_t *coords, const float *vals, const int *ranks,
+                          const double *U0, uint64_t seed, uint32_t flags, void *stream);
+
+/*
+ * ttmc_mode — sparse tensor-times-matrix chain of one mode (Algorithm 2, inner loop;
+ * Section III-C, eq. for Y_(1)):
+ *     Y_(n)(i_n, :) = sum over nonzeros z in slice i_n of x_z * kron_{m != n} U_m(i_m(z), :)
+ * using the context's current factors (FP32 copies, or BF16 with TUCKER_F_BF16_FACTORS).
+ *   Y   device float [I_n x P_n], caller-owned, fully overwritten (empty slices -> 0)
+ * Deterministic: no atomics; the same inputs give bitwise the same Y.
+ */
+TUCKER_API tucker_status ttmc_mode(tucker_ctx *c, int mode, float *Y, void *stream);
+
+/*
+ * qrp_leading — Householder QR with column pivoting truncated after k reflectors
+ * (Section III-D: A P = Q R, |r_11| >= |r_22| >= ..., H_j = I - 2 v v^T / (v^T v),
+ * v = a + sign(a_1) ||a|| e_1 with sign(0) = +1).  Column norms are downdated after
+ * each reflector and recomputed exactly when cancellation makes the downdate
+ * unreliable; the pivot is the largest trailing norm, the lowest index on ties.
+ *
+ *   A      device double, m x n, row stride lda >= n (read only)
+ *   k      number of reflectors, 0 <= k <= min(m, n)
+ *   Q      device double [m x k], row-major: Q = H_1 ... H_k [I_k; 0]
+ *   piv    device int64 [k]: original column index chosen at each step
+ *   rdiag  device double [k]: diagonal r_jj of R
+ *   work   device scratch of at least qrp_leading_work_bytes(m, n, k) bytes,
+ *          256-byte aligned, caller-owned; contents on entry are ignored
+ */
+TUCKER_API tucker_status qrp_leading(const double *A, int64_t m, int64_t n, int64_t lda, int k, double *Q,
+                          int64_t *piv, double *rdiag, void *work, size_t work_bytes, void *stream);
+TUCKER_API size_t qrp_leading_work_bytes(int64_t m, int64_t n, int k);
+
+/*
+ * hooi_iter — one sweep of Algorithm 2: for n = 1..N, Y_(n) by ttmc_mode and
+ * U_n <- the first R_n columns of Q from QRP of Y_(n) (of Y_(n) Y_(n)^T when
+ * P_n > I_n, unless TUCKER_F_QRP_DIRECT); then the core G = Y_(N) x_N U_N^T and
+ *     fit = 1 - sqrt(max(0, ||X||^2 - ||G||^2)) / ||X||.
+ *   fit_out  host double (the call then synchronises `stream`), or a device double
+ *            when the context was created with TUCKER_F_FIT_DEVICE; may be NULL
+ */
+TUCKER_API tucker_status hooi_iter(tucker_ctx *c, double *fit_out, void *stream);
+
+/*
+ * core_tensor — the core of the last sweep, G_(N) = U_N^T Y_(N) (Section III-B,
+ * eqs. ttm_ele and core_unfolded).  G: device double [R_1 * ... * R_N], C-order.
+ * TUCKER_ESTATE before the first hooi_iter or after tucker_set_factor.
+ */
+TUCKER_API tucker_status core_tensor(tucker_ctx *c, double *G, void *stream);
+
+/* Current factor U_n (FP64 master copy), device double [I_n x R_n]. */
+TUCKER_API tucker_status tucker_get_factor(tucker_ctx *c, int mode, double *U, void *stream);
+
+/* Replace factor U_n (device double [I_n x R_n], or host with TUCKER_F_HOST_INPUT);
+ * refreshes the FP32/BF16 copies that ttmc_mode reads. */
+TUCKER_API tucker_status tucker_set_factor(tucker_ctx *c, int mode, const double *U, void *stream);
+
+/*
+ * tucker_loss_grad — observed-entry loss of a Tucker model and its adjoint:
+ *     xhat_z = sum_r G[r] prod_m U_m(i_m(z), r_m),  e_z = xhat_z - x_z,
+ *     L = 1/2 sum_z e_z^2,
+ *     dL/dG = sum_z e_z kron_m U_m(i_m(z), :),
+ *     dL/dU_n(i, :) = sum_{z in slice i of mode n} e_z (G_(n) kron_{m != n} U_m(i_m(z), :)^T)
+ * over the context's (coalesced) nonzeros, in FP32; Kronecker rows are recomputed,
+ * never stored.  The gradient of U_n is a TTMc of the residuals contracted with G_(n).
+ *   U     host array of N device pointers, float [I_m x R_m]
+ *   G     device float [prod R], C-order
+ *   loss  device double [1]
+ *   dU    host array of N device pointers, float [I_m x R_m], overwritten
+ *   dG    device float [prod R], overwritten
+ * Deterministic (fixed reduction trees, no atomics on values).
+ */
+TUCKER_API tucker_status tucker_loss_grad(tucker_ctx *c, const float *const *U, const float *G, double *loss,
+                               float *const *dU, float *dG, void *stream);
+
+/* Number of nonzeros after coalescing, and ||X||_F^2 (FP64). */
+TUCKER_API int64_t tucker_nnz(const tucker_ctx *c);
+TUCKER_API double tucker_norm2(const tucker_ctx *c);
+
+/* Synchronise `stream` and report (then clear) the latched device error word. */
+TUCKER_API tucker_status tucker_sync_status(tucker_ctx *c, void *stream);
+
+/* Release every device and host resource of the context (NULL is a no-op).
+ * Synchronises the context's internal work first. */
+TUCKER_API void tucker_free(tucker_ctx *c);
+
+TUCKER_API const char *tucker_status_str(tucker_status s);
+/* Text of the last error recorded on this context ("" if none); valid until the next call. */
+TUCKER_API const char *tucker_last_error(const tucker_ctx *c);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TUCKER_H */

@@ -1,0 +1,360 @@
+// C-ABI entry points of libtucker (declared in include/tucker.h) and the HOOI driver
+// of Algorithm 2.  Host code only orchestrates: every step of the method runs in the
+// kernels of reorder.cu (K-a), ttmc.cu (K-b), qrp.cu (K-c), core.cu (K-d) and
+// adjoint.cu (K-e).
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "internal.cuh"
+
+using tk::Ctx;
+
+struct tucker_ctx {
+  Ctx c;
+};
+
+namespace tk {
+
+__global__ void f64_to_f32_kernel(const double *in, int64_t n, float *out32, __nv_bfloat16 *out16) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = in[i];
+    out32[i] = __double2float_rn(v);
+    if (out16) out16[i] = __double2bfloat16(v);
+  }
+}
+
+void refresh_factor_copies(Ctx *c, int m, cudaStream_t s) {
+  const int64_t n = c->dims[m] * c->ranks[m];
+  const unsigned b = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4096));
+  f64_to_f32_kernel<<<b, 256, 0, s>>>(c->U64[m], n, c->U32[m], c->U16[m]);
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014) as a counter-based generator; Box-Muller for N(0,1).
+__device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void gaussian_kernel(uint64_t seed, int mode, int64_t n, double *out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t base = seed * 0x2545F4914F6CDD1Dull + ((uint64_t)mode << 48) + 2ull * (uint64_t)i;
+    const double u1 = ((splitmix64(base) >> 11) + 1.0) * (1.0 / 9007199254740993.0);  // (0, 1]
+    const double u2 = (splitmix64(base + 1) >> 11) * (1.0 / 9007199254740992.0);      // [0, 1)
+    out[i] = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+  }
+}
+
+static tucker_status check_err_word(Ctx *c, cudaStream_t s) {
+  uint32_t bits = 0;
+  TK_CUDA(cudaMemcpyAsync(&bits, c->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  TK_CUDA(cudaStreamSynchronize(s));
+  if (bits) {
+    TK_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(uint32_t), s));
+    if (bits & kErrTimeout) {
+      c->last_error = "a bounded device-side wait gave up";
+      return TUCKER_ETIMEOUT;
+    }
+    c->last_error = "device-side input check failed";
+    return TUCKER_EINVAL;
+  }
+  return TUCKER_OK;
+}
+
+static int qrp_n_cols(const Ctx *c, int n) {
+  const int64_t I = c->dims[n], P = c->mode[n].P;
+  const bool fat = P > I && !(c->flags & TUCKER_F_QRP_DIRECT);
+  return (int)(fat ? I : P);
+}
+
+static tucker_status init_impl(Ctx *c, const uint32_t *coords, const float *vals, const double *U0, uint64_t seed,
+                               cudaStream_t s) {
+  const int N = c->N;
+  TK_CUDA(cudaGetDevice(&c->device));
+  TK_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+  TK_CUDA(dev_alloc(c, &c->d_err, 4));
+  TK_CUDA(dev_alloc(c, &c->norm_dev, 2));
+  TK_CUDA(dev_alloc(c, &c->fit_dev, 1));
+  TK_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(uint32_t), s));
+
+  // inputs on the device
+  const uint32_t *dcoords = coords;
+  const float *dvals = vals;
+  uint32_t *stage_c = nullptr;
+  float *stage_v = nullptr;
+  const bool host = (c->flags & TUCKER_F_HOST_INPUT) != 0;
+  if (host && c->nnz_in > 0) {
+    TK_CUDA(dev_alloc(c, &stage_c, (size_t)c->nnz_in * N));
+    TK_CUDA(dev_alloc(c, &stage_v, (size_t)c->nnz_in));
+    TK_CUDA(cudaMemcpyAsync(stage_c, coords, sizeof(uint32_t) * (size_t)c->nnz_in * N, cudaMemcpyHostToDevice, s));
+    TK_CUDA(cudaMemcpyAsync(stage_v, vals, sizeof(float) * (size_t)c->nnz_in, cudaMemcpyHostToDevice, s));
+    dcoords = stage_c;
+    dvals = stage_v;
+  }
+  tucker_status st = build_sorted_copies(c, dcoords, dvals, s);
+  if (stage_c) {
+    cudaStreamSynchronize(s);
+    c->allocs.erase(std::find(c->allocs.begin(), c->allocs.end(), (void *)stage_c));
+    c->allocs.erase(std::find(c->allocs.begin(), c->allocs.end(), (void *)stage_v));
+    cudaFree(stage_c);
+    cudaFree(stage_v);
+  }
+  if (st != TUCKER_OK) return st;
+
+  // buffers sized for the largest mode
+  int64_t ymax = 1, carry_max = 1, gram_max = 1, Imax = 1, IRmax = 1;
+  size_t qbytes = 256;
+  for (int n = 0; n < N; ++n) {
+    const ModeCopy &mc = c->mode[n];
+    ymax = std::max(ymax, mc.I * mc.P);
+    carry_max = std::max(carry_max, mc.n_units * mc.P);
+    Imax = std::max(Imax, mc.I);
+    IRmax = std::max(IRmax, c->dims[n] * c->ranks[n]);
+    const int ncols = qrp_n_cols(c, n);
+    if (ncols == mc.I && mc.P > mc.I) gram_max = std::max(gram_max, mc.I * mc.I);
+    qbytes = std::max(qbytes, qrp_work_bytes(mc.I, ncols, c->ranks[n], c->num_sms));
+    // seeded initial factors run QRP on I_n x R_n
+    qbytes = std::max(qbytes, qrp_work_bytes(mc.I, c->ranks[n], c->ranks[n], c->num_sms));
+  }
+  int64_t PR = 1;
+  for (int n = 0; n < N; ++n) PR *= c->ranks[n];
+  TK_CUDA(dev_alloc(c, &c->Y, (size_t)ymax));
+  TK_CUDA(dev_alloc(c, &c->carry, (size_t)carry_max));
+  TK_CUDA(dev_alloc(c, &c->gram, (size_t)gram_max));
+  TK_CUDA(dev_alloc(c, &c->G, (size_t)PR));
+  TK_CUDA(dev_alloc(c, &c->core_part, core_part_elems(c->num_sms, c->mode[N - 1].P, c->ranks[N - 1])));
+  TK_CUDA(dev_alloc(c, &c->core_counter, 4));
+  TK_CUDA(cudaMemsetAsync(c->core_counter, 0, 16, s));
+  void *qbase = nullptr;
+  TK_CUDA(dev_alloc(c, &qbase, qbytes));
+  c->qw.V = static_cast<double *>(qbase);  // base pointer; bound per call
+  c->qw.bytes = qbytes;
+
+  // factors
+  for (int m = 0; m < N; ++m) {
+    const size_t n = (size_t)(c->dims[m] * c->ranks[m]);
+    TK_CUDA(dev_alloc(c, &c->U64[m], n));
+    TK_CUDA(dev_alloc(c, &c->U32[m], n));
+    if (c->flags & TUCKER_F_BF16_FACTORS) TK_CUDA(dev_alloc(c, &c->U16[m], n));
+  }
+  if (U0) {
+    size_t off = 0;
+    for (int m = 0; m < N; ++m) {
+      const size_t n = (size_t)(c->dims[m] * c->ranks[m]);
+      TK_CUDA(cudaMemcpyAsync(c->U64[m], U0 + off, n * sizeof(double),
+                              host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+      off += n;
+    }
+  } else {
+    double *g = nullptr;
+    TK_CUDA(dev_alloc(c, &g, (size_t)IRmax));
+    for (int m = 0; m < N; ++m) {
+      const int64_t n = c->dims[m] * c->ranks[m];
+      gaussian_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(seed, m, n, g);
+      QrpWork w;
+      qrp_bind_work(&w, c->qw.V, c->dims[m], c->ranks[m], c->ranks[m], c->num_sms);
+      st = qrp_run_f64(g, c->dims[m], c->ranks[m], c->ranks[m], c->ranks[m], c->U64[m], c->ranks[m], nullptr,
+                       nullptr, &w, c->num_sms, s);
+      if (st != TUCKER_OK) return st;
+    }
+    TK_CUDA(cudaStreamSynchronize(s));
+    c->allocs.erase(std::find(c->allocs.begin(), c->allocs.end(), (void *)g));
+    cudaFree(g);
+  }
+  for (int m = 0; m < N; ++m) refresh_factor_copies(c, m, s);
+  TK_CUDA(cudaGetLastError());
+  TK_CUDA(cudaStreamSynchronize(s));
+  return TUCKER_OK;
+}
+
+static tucker_status hooi_impl(Ctx *c, double *fit_out, cudaStream_t s) {
+  const int N = c->N;
+  for (int n = 0; n < N; ++n) {
+    const ModeCopy &mc = c->mode[n];
+    tucker_status st = launch_ttmc(c, n, c->Y, s);
+    if (st != TUCKER_OK) return st;
+    const int k = c->ranks[n];
+    const int ncols = qrp_n_cols(c, n);
+    QrpWork w;
+    qrp_bind_work(&w, c->qw.V, mc.I, ncols, k, c->num_sms);
+    if (ncols == mc.I && mc.P > mc.I) {
+      gram_f32(c->Y, mc.I, mc.P, c->gram, s);
+      st = qrp_run_f64(c->gram, mc.I, mc.I, mc.I, k, c->U64[n], k, nullptr, nullptr, &w, c->num_sms, s);
+    } else {
+      st = qrp_run_f32(c->Y, mc.I, mc.P, mc.P, k, c->U64[n], k, nullptr, nullptr, &w, c->num_sms, s);
+    }
+    if (st != TUCKER_OK) return st;
+    refresh_factor_copies(c, n, s);
+  }
+  launch_core(c, c->Y, c->U64[N - 1], c->G, s);
+  TK_CUDA(cudaGetLastError());
+  c->G_valid = true;
+  ++c->sweeps;
+  if (fit_out) {
+    if (c->flags & TUCKER_F_FIT_DEVICE) {
+      TK_CUDA(cudaMemcpyAsync(fit_out, c->fit_dev, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    } else {
+      TK_CUDA(cudaMemcpyAsync(fit_out, c->fit_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+      return check_err_word(c, s);
+    }
+  }
+  return TUCKER_OK;
+}
+
+}  // namespace tk
+
+// ============================================================================ C ABI
+extern "C" {
+
+const char *tucker_status_str(tucker_status s) {
+  switch (s) {
+    case TUCKER_OK: return "ok";
+    case TUCKER_EINVAL: return "invalid argument";
+    case TUCKER_ERANK: return "rank out of range";
+    case TUCKER_ENOMEM: return "out of memory";
+    case TUCKER_ECUDA: return "CUDA error";
+    case TUCKER_ETIMEOUT: return "device wait timed out";
+    case TUCKER_ESTATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+const char *tucker_last_error(const tucker_ctx *c) { return c ? c->c.last_error.c_str() : ""; }
+
+int64_t tucker_nnz(const tucker_ctx *c) { return c ? c->c.nnz : -1; }
+double tucker_norm2(const tucker_ctx *c) { return c ? c->c.norm2 : 0.0; }
+
+void tucker_free(tucker_ctx *c) {
+  if (!c) return;
+  cudaDeviceSynchronize();
+  for (void *p : c->c.allocs) cudaFree(p);
+  delete c;
+}
+
+tucker_status tucker_init(tucker_ctx **out, int order, const int64_t *dims, int64_t nnz, const uint32_t *coords,
+                          const float *vals, const int *ranks, const double *U0, uint64_t seed, uint32_t flags,
+                          void *stream) {
+  if (!out) return TUCKER_EINVAL;
+  *out = nullptr;
+  if (order < 2 || order > tk::kMaxOrder || !dims || !ranks || nnz < 0 || nnz > 0x7fffffffLL) return TUCKER_EINVAL;
+  if (nnz > 0 && (!coords || !vals)) return TUCKER_EINVAL;
+  int64_t PR = 1;
+  for (int m = 0; m < order; ++m) {
+    if (dims[m] < 1 || dims[m] > 0x7fffffffLL) return TUCKER_EINVAL;
+    if (ranks[m] < 1 || ranks[m] > dims[m] || ranks[m] > 64) return TUCKER_ERANK;
+    PR *= ranks[m];
+    if (PR > (1 << 20)) return TUCKER_ERANK;
+  }
+  for (int n = 0; n < order; ++n) {
+    int64_t P = 1;
+    for (int m = 0; m < order; ++m)
+      if (m != n) P *= ranks[m];
+    const bool fat = P > dims[n];
+    const bool direct = (flags & TUCKER_F_QRP_DIRECT) != 0;
+    if ((!fat || direct) && ranks[n] > P) return TUCKER_ERANK;  // k <= min(I_n, P_n)
+  }
+  tucker_ctx *h = new (std::nothrow) tucker_ctx();
+  if (!h) return TUCKER_ENOMEM;
+  Ctx *c = &h->c;
+  c->N = order;
+  for (int m = 0; m < order; ++m) {
+    c->dims[m] = dims[m];
+    c->ranks[m] = ranks[m];
+  }
+  c->flags = flags;
+  c->nnz_in = nnz;
+  tk::reset_alloc_counter();
+  tucker_status st = tk::init_impl(c, coords, vals, U0, seed, static_cast<cudaStream_t>(stream));
+  if (st != TUCKER_OK) {
+    // keep the message for the caller through a temporary context? The context is
+    // released; the status code carries the failure.
+    tucker_free(h);
+    return st;
+  }
+  *out = h;
+  return TUCKER_OK;
+}
+
+tucker_status ttmc_mode(tucker_ctx *h, int mode, float *Y, void *stream) {
+  if (!h || !Y || mode < 0 || mode >= h->c.N) return TUCKER_EINVAL;
+  if (reinterpret_cast<uintptr_t>(Y) % 16) return TUCKER_EINVAL;
+  return tk::launch_ttmc(&h->c, mode, Y, static_cast<cudaStream_t>(stream));
+}
+
+tucker_status hooi_iter(tucker_ctx *h, double *fit_out, void *stream) {
+  if (!h) return TUCKER_EINVAL;
+  return tk::hooi_impl(&h->c, fit_out, static_cast<cudaStream_t>(stream));
+}
+
+tucker_status core_tensor(tucker_ctx *h, double *G, void *stream) {
+  if (!h || !G) return TUCKER_EINVAL;
+  Ctx *c = &h->c;
+  if (!c->G_valid) return TUCKER_ESTATE;
+  int64_t PR = 1;
+  for (int m = 0; m < c->N; ++m) PR *= c->ranks[m];
+  TK_CUDA(cudaMemcpyAsync(G, c->G, sizeof(double) * (size_t)PR, cudaMemcpyDeviceToDevice,
+                          static_cast<cudaStream_t>(stream)));
+  return TUCKER_OK;
+}
+
+tucker_status tucker_get_factor(tucker_ctx *h, int mode, double *U, void *stream) {
+  if (!h || !U || mode < 0 || mode >= h->c.N) return TUCKER_EINVAL;
+  Ctx *c = &h->c;
+  TK_CUDA(cudaMemcpyAsync(U, c->U64[mode], sizeof(double) * (size_t)(c->dims[mode] * c->ranks[mode]),
+                          cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream)));
+  return TUCKER_OK;
+}
+
+tucker_status tucker_set_factor(tucker_ctx *h, int mode, const double *U, void *stream) {
+  if (!h || !U || mode < 0 || mode >= h->c.N) return TUCKER_EINVAL;
+  Ctx *c = &h->c;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool host = (c->flags & TUCKER_F_HOST_INPUT) != 0;
+  TK_CUDA(cudaMemcpyAsync(c->U64[mode], U, sizeof(double) * (size_t)(c->dims[mode] * c->ranks[mode]),
+                          host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+  tk::refresh_factor_copies(c, mode, s);
+  TK_CUDA(cudaGetLastError());
+  c->G_valid = false;
+  return TUCKER_OK;
+}
+
+tucker_status tucker_sync_status(tucker_ctx *h, void *stream) {
+  if (!h) return TUCKER_EINVAL;
+  return tk::check_err_word(&h->c, static_cast<cudaStream_t>(stream));
+}
+
+size_t qrp_leading_work_bytes(int64_t m, int64_t n, int k) {
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return tk::qrp_work_bytes(m, n, k, sms);
+}
+
+tucker_status qrp_leading(const double *A, int64_t m, int64_t n, int64_t lda, int k, double *Q, int64_t *piv,
+                          double *rdiag, void *work, size_t work_bytes, void *stream) {
+  if (m < 0 || n < 0 || lda < n || k < 0) return TUCKER_EINVAL;
+  if (k > m || k > n) return TUCKER_ERANK;
+  if (k > 64) return TUCKER_ERANK;
+  if (k == 0) return TUCKER_OK;
+  if (!A || !Q || !work) return TUCKER_EINVAL;
+  if (reinterpret_cast<uintptr_t>(work) % 256) return TUCKER_EINVAL;
+  if (work_bytes < qrp_leading_work_bytes(m, n, k)) return TUCKER_EINVAL;
+  int dev = 0, sms = 1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return TUCKER_ECUDA;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return TUCKER_ECUDA;
+  tk::QrpWork w;
+  tk::qrp_bind_work(&w, work, m, n, k, sms);
+  return tk::qrp_run_f64(A, m, n, lda, k, Q, k, piv, rdiag, &w, sms, static_cast<cudaStream_t>(stream));
+}
+
+tucker_status tucker_loss_grad(tucker_ctx *h, const float *const *U, const float *G, double *loss, float *const *dU,
+                               float *dG, void *stream) {
+  if (!h || !U || !G || !loss || !dU || !dG) return TUCKER_EINVAL;
+  for (int m = 0; m < h->c.N; ++m)
+    if (!U[m] || !dU[m]) return TUCKER_EINVAL;
+  return tk::launch_loss_grad(&h->c, U, G, loss, dU, dG, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

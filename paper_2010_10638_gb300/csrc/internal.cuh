@@ -1,0 +1,150 @@
+// Internal declarations shared by the translation units of libtucker.
+// Not part of the public ABI (see include/tucker.h).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/tucker.h"
+
+namespace tk {
+
+constexpr int kMaxOrder = 8;
+constexpr uint32_t kErrCoord = 1u;    // a coordinate >= its dimension
+constexpr uint32_t kErrValue = 2u;    // a non-finite value
+constexpr uint32_t kErrTimeout = 4u;  // a bounded device-side wait gave up
+
+// Per-mode sorted copy of the nonzeros (a CSF root level over the non-empty slices)
+// and the work-unit table of the TTMc kernel.
+struct ModeCopy {
+  int64_t I = 0;   // rows of Y_(n)
+  int64_t P = 0;   // columns of Y_(n)
+  int64_t S = 0;   // non-empty slices
+  int nother = 0;  // N - 1
+  int other[kMaxOrder] = {};           // remaining modes, ascending
+  uint32_t *idx[kMaxOrder] = {};       // idx[t][e]: coordinate of mode other[t] of sorted nonzero e
+  float *val = nullptr;                // value of sorted nonzero e
+  uint32_t *sptr = nullptr;            // [S+1] first sorted position of each non-empty slice
+  uint32_t *sid = nullptr;             // [S] row of Y_(n) of each non-empty slice
+  uint32_t *empty = nullptr;           // [n_empty] rows with no nonzero
+  int64_t n_empty = 0;
+  int chunk = 0;                       // nominal nonzeros per work unit
+  uint32_t *unit_e0 = nullptr;         // [n_units] first sorted position of each unit
+  uint32_t *unit_k0 = nullptr;         // [n_units] slice containing that position
+  int32_t *unit_slot = nullptr;        // [n_units] -1: whole slices -> Y; >= 0: partial row slot
+  int64_t n_units = 0;
+  uint32_t *long_k = nullptr;          // [n_long] slices longer than `chunk`
+  uint32_t *long_u0 = nullptr;         // [n_long] their first unit (= first partial slot)
+  uint32_t *long_np = nullptr;         // [n_long] their number of units
+  int64_t n_long = 0;
+};
+
+// Workspace of the QR with column pivoting (one set, sized for the largest mode).
+struct QrpWork {
+  double *V = nullptr;       // m x k reflectors, V[i*k + j]
+  double *F = nullptr;       // n x k, F[c*k + j]
+  double *part = nullptr;    // nb x (n + k) block partial sums
+  double *vn = nullptr;      // n trailing squared norms (current column order)
+  double *vref = nullptr;    // n squared norms at their last exact computation
+  int *perm = nullptr;       // n current column order (original indices)
+  int *flag = nullptr;       // n columns whose norm must be recomputed
+  double *T = nullptr;       // k x k triangular factor of the compact WY form
+  double *M = nullptr;       // k x k, T * V[0:k, :]^T
+  double *scal = nullptr;    // scalars: [0] tau, [1] beta, [2] v_jj, [3..] misc
+  int *iscal = nullptr;      // int scalars: [0] pivot, [1] number of flagged columns, [2..3] counters
+  unsigned *counter = nullptr;  // last-block counters
+  size_t bytes = 0;
+};
+
+struct Ctx {
+  int N = 0;
+  int64_t dims[kMaxOrder] = {};
+  int ranks[kMaxOrder] = {};
+  uint32_t flags = 0;
+  int64_t nnz_in = 0;
+  int64_t nnz = 0;           // after coalescing
+  double norm2 = 0.0;        // ||X||^2 over coalesced values
+  int num_sms = 0;
+  int device = 0;
+
+  uint32_t *coords = nullptr;  // coalesced [N][nnz] (lexicographic order)
+  float *vals = nullptr;       // coalesced values (FP32 rounding of the FP64 sums)
+  ModeCopy mode[kMaxOrder];
+
+  double *U64[kMaxOrder] = {};        // FP64 master factors
+  float *U32[kMaxOrder] = {};         // FP32 copies read by the TTMc
+  __nv_bfloat16 *U16[kMaxOrder] = {}; // BF16 copies (TUCKER_F_BF16_FACTORS)
+
+  float *Y = nullptr;          // TTMc output of the current mode (max I_n * P_n floats)
+  float *carry = nullptr;      // partial rows of split slices (max n_units * P_n floats)
+  double *gram = nullptr;      // Y Y^T for fat unfoldings
+  double *G = nullptr;         // core tensor of the last sweep
+  double *fit_dev = nullptr;   // fit of the last sweep (device)
+  double *norm_dev = nullptr;  // [0] ||X||^2, [1] ||G||^2
+  double *core_part = nullptr; // block partials of the core GEMM
+  unsigned *core_counter = nullptr;
+  bool G_valid = false;
+  int sweeps = 0;
+
+  QrpWork qw;
+  uint32_t *d_err = nullptr;   // latched device error bits
+
+  std::vector<void *> allocs;  // every device allocation, freed by tucker_free
+  std::string last_error;
+};
+
+// ---- allocation (host-side failure injection for tests: TUCKER_FAIL_ALLOC_AT=k fails the k-th)
+cudaError_t dev_alloc(Ctx *c, void **p, size_t bytes);
+template <typename T>
+cudaError_t dev_alloc(Ctx *c, T **p, size_t count) {
+  return dev_alloc(c, reinterpret_cast<void **>(p), count * sizeof(T));
+}
+void reset_alloc_counter();
+
+// ---- scan (exclusive, uint32) over n elements; `tmp` must hold scan_tmp_elems(n) words
+size_t scan_tmp_elems(int64_t n);
+void exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *tmp, cudaStream_t s);
+
+// ---- K-a: reorder (reorder.cu)
+tucker_status build_sorted_copies(Ctx *c, const uint32_t *coords, const float *vals, cudaStream_t s);
+
+// ---- K-b: TTMc (ttmc.cu)
+tucker_status launch_ttmc(Ctx *c, int mode, float *Y, cudaStream_t s);
+
+// ---- K-c: QRP (qrp.cu)
+size_t qrp_work_bytes(int64_t m, int64_t n, int k, int nb);
+void qrp_bind_work(QrpWork *w, void *base, int64_t m, int64_t n, int k, int nb);
+// A is m x n (row stride lda) of type float or double; writes Q (m x k, row stride ldq),
+// piv (int64, may be null), rdiag (may be null).
+tucker_status qrp_run_f64(const double *A, int64_t m, int64_t n, int64_t lda, int k, double *Q, int64_t ldq,
+                          int64_t *piv, double *rdiag, QrpWork *w, int nb, cudaStream_t s);
+tucker_status qrp_run_f32(const float *A, int64_t m, int64_t n, int64_t lda, int k, double *Q, int64_t ldq,
+                          int64_t *piv, double *rdiag, QrpWork *w, int nb, cudaStream_t s);
+void gram_f32(const float *Y, int64_t m, int64_t n, double *S, cudaStream_t s);
+int qrp_blocks(int num_sms, int64_t m);
+
+// ---- K-d: core tensor and fit (core.cu)
+void launch_core(Ctx *c, const float *Y, const double *U, double *G, cudaStream_t s);
+size_t core_part_elems(int num_sms, int64_t P, int R);
+
+// ---- factor copies / misc (api.cu)
+void refresh_factor_copies(Ctx *c, int mode, cudaStream_t s);
+
+// ---- K-e: adjoint (adjoint.cu)
+tucker_status launch_loss_grad(Ctx *c, const float *const *U, const float *G, double *loss, float *const *dU,
+                               float *dG, cudaStream_t s);
+
+}  // namespace tk
+
+#define TK_CUDA(call)                                                     \
+  do {                                                                    \
+    cudaError_t e__ = (call);                                             \
+    if (e__ != cudaSuccess) {                                             \
+      c->last_error = std::string(#call) + ": " + cudaGetErrorString(e__); \
+      return e__ == cudaErrorMemoryAllocation ? TUCKER_ENOMEM : TUCKER_ECUDA; \
+    }                                                                     \
+  } while (0)

@@ -1,0 +1,594 @@
+// K-a: input validation, duplicate coalescing and the per-mode sorted copies.
+//
+// The paper stores the sparse tensor in COO form (Section III-A, Table I) and runs the
+// Kronecker accumulation of Algorithm 2 over its nonzeros.  On the GPU every mode gets
+// its own copy of the nonzeros sorted by that mode's index, so that the nonzeros of a
+// slice (one row of Y_(n)) are contiguous and can be reduced without atomics:
+//   - LSD radix passes (8-bit digits, stable: histogram -> exclusive scan -> scatter
+//     ranked with warp match) sort by the full coordinate, mode 1 most significant;
+//   - equal neighbours are summed in FP64 (input order) into one nonzero;
+//   - per mode: stable radix sort by i_n, gather of the other modes' indices and the
+//     values (structure of arrays), offsets of the non-empty slices (a CSF root
+//     level), the list of empty rows, and a table of work units of about `chunk`
+//     nonzeros: runs of whole short slices, or pieces of a long slice whose partial
+//     rows are combined by a second pass.
+#include <algorithm>
+#include <cstdlib>
+
+#include "internal.cuh"
+
+namespace tk {
+
+// ----------------------------------------------------------------------------- allocation
+static int g_alloc_count = 0;
+void reset_alloc_counter() { g_alloc_count = 0; }
+
+cudaError_t dev_alloc(Ctx *c, void **p, size_t bytes) {
+  *p = nullptr;
+  ++g_alloc_count;
+  const char *f = std::getenv("TUCKER_FAIL_ALLOC_AT");
+  if (f && std::atoi(f) == g_alloc_count) return cudaErrorMemoryAllocation;
+  if (bytes == 0) bytes = 256;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaSuccess) c->allocs.push_back(*p);
+  else (void)cudaGetLastError();
+  return e;
+}
+
+static void dev_release(Ctx *c, void *p) {
+  if (!p) return;
+  auto it = std::find(c->allocs.begin(), c->allocs.end(), p);
+  if (it != c->allocs.end()) c->allocs.erase(it);
+  cudaFree(p);
+}
+
+// ----------------------------------------------------------------------------- scan
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__global__ void __launch_bounds__(kScanThreads) scan_block_kernel(const uint32_t *in, uint32_t *out, int64_t n,
+                                                                   uint32_t *block_sums) {
+  __shared__ uint32_t warp_tot[32];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)tid * kScanItems;
+  uint32_t v[kScanItems];
+  uint32_t s = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    v[i] = (base + i < n) ? in[base + i] : 0u;
+    s += v[i];
+  }
+  uint32_t incl = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) warp_tot[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t t = warp_tot[lane];
+    uint32_t ti = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t u = __shfl_up_sync(0xffffffffu, ti, o);
+      if (lane >= o) ti += u;
+    }
+    warp_tot[lane] = ti - t;  // exclusive prefix of warp totals
+    if (lane == 31 && block_sums) block_sums[blockIdx.x] = ti;
+  }
+  __syncthreads();
+  uint32_t run = warp_tot[w] + incl - s;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    if (base + i < n) out[base + i] = run;
+    run += v[i];
+  }
+}
+
+__global__ void scan_add_kernel(uint32_t *out, int64_t n, const uint32_t *block_off) {
+  const uint32_t add = block_off[blockIdx.x];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  for (int i = threadIdx.x; i < kScanTile; i += blockDim.x)
+    if (base + i < n) out[base + i] += add;
+}
+
+static int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+size_t scan_tmp_elems(int64_t n) {
+  size_t t = 0;
+  int64_t m = n;
+  do {
+    m = cdiv(m, kScanTile);
+    t += (size_t)m + 1;
+  } while (m > 1);
+  return t + 1;
+}
+
+// exclusive scan; the grand total goes to *total (device) when total != nullptr
+static void scan_rec(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *tmp, uint32_t *total, cudaStream_t s) {
+  if (n <= 0) return;
+  int64_t nb = cdiv(n, kScanTile);
+  if (nb == 1) {
+    scan_block_kernel<<<1, kScanThreads, 0, s>>>(in, out, n, total);
+    return;
+  }
+  scan_block_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, tmp);
+  scan_rec(tmp, tmp, nb, tmp + nb + 1, total, s);
+  scan_add_kernel<<<(unsigned)nb, 256, 0, s>>>(out, n, tmp);
+}
+
+void exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *tmp, cudaStream_t s) {
+  scan_rec(in, out, n, tmp, nullptr, s);
+}
+
+static void exclusive_scan_total(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *tmp, uint32_t *total,
+                                 cudaStream_t s) {
+  scan_rec(in, out, n, tmp, total, s);
+}
+
+// ----------------------------------------------------------------------------- validation
+__global__ void validate_kernel(int N, int64_t nnz, const uint32_t *coords, const float *vals, const int64_t *dims_in,
+                                uint32_t *err) {
+  __shared__ int64_t dims[kMaxOrder];
+  if (threadIdx.x < N) dims[threadIdx.x] = dims_in[threadIdx.x];
+  __syncthreads();
+  uint32_t bits = 0;
+  for (int64_t z = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; z < nnz; z += (int64_t)gridDim.x * blockDim.x) {
+    for (int m = 0; m < N; ++m)
+      if ((int64_t)coords[(int64_t)m * nnz + z] >= dims[m]) bits |= kErrCoord;
+    if (!isfinite(vals[z])) bits |= kErrValue;
+  }
+  bits = __reduce_or_sync(0xffffffffu, bits);
+  if ((threadIdx.x & 31) == 0 && bits) atomicOr(err, bits);
+}
+
+// ----------------------------------------------------------------------------- radix passes
+constexpr int kRsThreads = 256;
+constexpr int kRsWarps = kRsThreads / 32;
+constexpr int kRsPerWarp = 512;
+constexpr int kRsTile = kRsWarps * kRsPerWarp;
+
+__global__ void __launch_bounds__(kRsThreads) radix_hist_kernel(const uint32_t *key, const uint32_t *perm, int64_t n,
+                                                                int shift, uint32_t *hist) {
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kRsTile;
+  for (int i = threadIdx.x; i < kRsTile; i += kRsThreads) {
+    int64_t e = base + i;
+    if (e < n) {
+      uint32_t k = key[perm ? perm[e] : (uint32_t)e];
+      atomicAdd(&h[(k >> shift) & 255u], 1u);
+    }
+  }
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kRsThreads) radix_scatter_kernel(const uint32_t *key, const uint32_t *perm_in,
+                                                                   uint32_t *perm_out, int64_t n, int shift,
+                                                                   const uint32_t *hist_off) {
+  __shared__ uint32_t wh[kRsWarps][256];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  for (int i = tid; i < kRsWarps * 256; i += kRsThreads) wh[i / 256][i % 256] = 0;
+  __syncthreads();
+  const int64_t wbase = (int64_t)blockIdx.x * kRsTile + (int64_t)w * kRsPerWarp;
+  for (int st = 0; st < kRsPerWarp / 32; ++st) {
+    int64_t e = wbase + st * 32 + lane;
+    if (e < n) {
+      uint32_t k = key[perm_in ? perm_in[e] : (uint32_t)e];
+      atomicAdd(&wh[w][(k >> shift) & 255u], 1u);
+    }
+  }
+  __syncthreads();
+  {  // thread tid owns digit tid: running offset over the warps of this block
+    uint32_t run = hist_off[(int64_t)tid * gridDim.x + blockIdx.x];
+    for (int ww = 0; ww < kRsWarps; ++ww) {
+      uint32_t cnt = wh[ww][tid];
+      wh[ww][tid] = run;
+      run += cnt;
+    }
+  }
+  __syncthreads();
+  const uint32_t lt = (1u << lane) - 1u;
+  for (int st = 0; st < kRsPerWarp / 32; ++st) {
+    int64_t e = wbase + st * 32 + lane;
+    bool valid = e < n;
+    uint32_t src = 0, d = 256u + lane;
+    if (valid) {
+      src = perm_in ? perm_in[e] : (uint32_t)e;
+      d = (key[src] >> shift) & 255u;
+    }
+    uint32_t peers = __match_any_sync(0xffffffffu, d);
+    uint32_t rank = __popc(peers & lt);
+    uint32_t pos = valid ? wh[w][d] + rank : 0u;
+    __syncwarp();
+    if (valid && rank == 0) wh[w][d] += __popc(peers);
+    __syncwarp();
+    if (valid) perm_out[pos] = src;
+  }
+}
+
+static int bits_for(int64_t maxval) {
+  int b = 0;
+  while (b < 63 && (maxval >> b) > 0) ++b;
+  return b;
+}
+
+// Stable sort of the permutation by key[perm[e]] (all bits of key < 2^bits).
+// On return *perm points at the sorted permutation (one of pa / pb), or stays
+// nullptr (identity) when no pass was needed.
+static void radix_sort_perm(const uint32_t *key, int bits, int64_t n, uint32_t **perm, uint32_t *pa, uint32_t *pb,
+                            uint32_t *hist, uint32_t *tmp, cudaStream_t s) {
+  if (n <= 1) return;
+  const int64_t nb = cdiv(n, kRsTile);
+  for (int shift = 0; shift < bits; shift += 8) {
+    uint32_t *out = (*perm == pa) ? pb : pa;
+    radix_hist_kernel<<<(unsigned)nb, kRsThreads, 0, s>>>(key, *perm, n, shift, hist);
+    exclusive_scan_u32(hist, hist, 256 * nb, tmp, s);
+    radix_scatter_kernel<<<(unsigned)nb, kRsThreads, 0, s>>>(key, *perm, out, n, shift, hist);
+    *perm = out;
+  }
+}
+
+// ----------------------------------------------------------------------------- coalescing
+__global__ void mark_new_kernel(int N, int64_t n, const uint32_t *coords, const uint32_t *perm, uint32_t *flag) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t f = 1;
+    if (e > 0) {
+      uint32_t a = perm ? perm[e] : (uint32_t)e, b = perm ? perm[e - 1] : (uint32_t)(e - 1);
+      f = 0;
+      for (int m = 0; m < N; ++m)
+        if (coords[(int64_t)m * n + a] != coords[(int64_t)m * n + b]) {
+          f = 1;
+          break;
+        }
+    }
+    flag[e] = f;
+  }
+}
+
+// One thread per group of equal coordinates: FP64 sum in sorted (= input) order.
+__global__ void coalesce_kernel(int N, int64_t n, const uint32_t *coords, const float *vals, const uint32_t *perm,
+                                const uint32_t *flag, const uint32_t *uid, int64_t nout, uint32_t *out_coords,
+                                float *out_vals, double *out_sq) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    if (!flag[e]) continue;
+    const uint32_t u = uid[e];
+    const uint32_t p = perm ? perm[e] : (uint32_t)e;
+    for (int m = 0; m < N; ++m) out_coords[(int64_t)m * nout + u] = coords[(int64_t)m * n + p];
+    double s = (double)vals[p];
+    for (int64_t e2 = e + 1; e2 < n && !flag[e2]; ++e2) s += (double)vals[perm ? perm[e2] : (uint32_t)e2];
+    out_vals[u] = (float)s;
+    out_sq[u] = s * s;
+  }
+}
+
+constexpr int kRedBlocks = 256;
+__global__ void reduce_f64_partial(const double *in, int64_t n, double *part) {
+  __shared__ double sm[256];
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    s += in[i];
+  sm[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
+}
+__global__ void reduce_f64_final(const double *part, int np, double *out) {
+  __shared__ double sm[256];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) s += part[i];
+  sm[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sm[0];
+}
+
+// ----------------------------------------------------------------------------- per-mode copies
+struct GatherArgs {
+  int nother;
+  const uint32_t *src[kMaxOrder];
+  uint32_t *dst[kMaxOrder];
+};
+
+__global__ void gather_mode_kernel(int64_t n, const uint32_t *perm, GatherArgs g, const uint32_t *rowsrc,
+                                   uint32_t *row, const float *vsrc, float *vdst) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t p = perm ? perm[e] : (uint32_t)e;
+    row[e] = rowsrc[p];
+    vdst[e] = vsrc[p];
+    for (int t = 0; t < g.nother; ++t) g.dst[t][e] = g.src[t][p];
+  }
+}
+
+__global__ void slice_start_kernel(int64_t n, const uint32_t *row, uint32_t *flag) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    flag[e] = (e == 0 || row[e] != row[e - 1]) ? 1u : 0u;
+}
+
+__global__ void slice_write_kernel(int64_t n, const uint32_t *row, const uint32_t *flag, const uint32_t *kid,
+                                   uint32_t *sptr, uint32_t *sid, uint32_t *present, int64_t S) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    if (flag[e]) {
+      const uint32_t k = kid[e];
+      sptr[k] = (uint32_t)e;
+      sid[k] = row[e];
+      present[row[e]] = 1u;
+    }
+    if (e == 0) sptr[S] = (uint32_t)n;
+  }
+}
+
+__global__ void invert_flag_kernel(int64_t n, const uint32_t *present, uint32_t *absent) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    absent[i] = present[i] ? 0u : 1u;
+}
+
+__global__ void compact_kernel(int64_t n, const uint32_t *flag, const uint32_t *pos, uint32_t *out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (flag[i]) out[pos[i]] = (uint32_t)i;
+}
+
+// units contributed by each non-empty slice k: pieces of a long slice, or 1 for the
+// first slice of a run of short slices (a new run starts at a long slice, after a long
+// slice, and where the slice start crosses into a new multiple of `chunk`).
+__global__ void unit_count_kernel(int64_t S, const uint32_t *sptr, uint32_t chunk, uint32_t *nu, uint32_t *islong) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < S; k += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t b = sptr[k], len = sptr[k + 1] - b;
+    const bool lng = len > chunk;
+    bool head = (k == 0) || lng;
+    if (k > 0) {
+      const uint32_t pb = sptr[k - 1], plen = b - pb;
+      head = head || plen > chunk || (b / chunk) != (pb / chunk);
+    }
+    nu[k] = lng ? (len + chunk - 1) / chunk : (head ? 1u : 0u);
+    islong[k] = lng ? 1u : 0u;
+  }
+}
+
+__global__ void unit_write_kernel(int64_t S, const uint32_t *sptr, uint32_t chunk, const uint32_t *nu,
+                                  const uint32_t *uoff, const uint32_t *islong, const uint32_t *lid,
+                                  uint32_t *unit_e0, uint32_t *unit_k0, int32_t *unit_slot, uint32_t *long_k,
+                                  uint32_t *long_u0, uint32_t *long_np) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < S; k += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t n = nu[k];
+    if (n == 0) continue;
+    const uint32_t u0 = uoff[k];
+    if (islong[k]) {
+      for (uint32_t p = 0; p < n; ++p) {
+        unit_e0[u0 + p] = sptr[k] + p * chunk;
+        unit_k0[u0 + p] = (uint32_t)k;
+        unit_slot[u0 + p] = (int32_t)(u0 + p);
+      }
+      const uint32_t l = lid[k];
+      long_k[l] = (uint32_t)k;
+      long_u0[l] = u0;
+      long_np[l] = n;
+    } else {
+      unit_e0[u0] = sptr[k];
+      unit_k0[u0] = (uint32_t)k;
+      unit_slot[u0] = -1;
+    }
+  }
+}
+
+static int pick_chunk(int64_t nnz, int num_sms) {
+  const char *f = std::getenv("TUCKER_TTMC_CHUNK");
+  if (f) {
+    int v = std::atoi(f);
+    if (v >= 32 && v <= (1 << 20) && (v % 32) == 0) return v;
+  }
+  int64_t target = nnz / ((int64_t)num_sms * 8);
+  int chunk = 256;
+  while (chunk < 2048 && (int64_t)chunk * 2 <= target) chunk *= 2;
+  return chunk;
+}
+
+// RAII holder for temporaries of the build
+struct Temps {
+  Ctx *c;
+  std::vector<void *> ptrs;
+  explicit Temps(Ctx *cc) : c(cc) {}
+  template <typename T>
+  cudaError_t get(T **p, size_t count) {
+    cudaError_t e = dev_alloc(c, p, count);
+    if (e == cudaSuccess) ptrs.push_back(*p);
+    return e;
+  }
+  ~Temps() {
+    for (void *p : ptrs) dev_release(c, p);
+  }
+};
+
+static unsigned grid_for(int64_t n, int threads = 256) {
+  int64_t b = cdiv(n, threads);
+  if (b < 1) b = 1;
+  if (b > 65535LL * 8) b = 65535LL * 8;
+  return (unsigned)b;
+}
+
+#define TK_TRY(call)                                                        \
+  do {                                                                      \
+    cudaError_t e__ = (call);                                               \
+    if (e__ != cudaSuccess) {                                               \
+      c->last_error = std::string(#call) + ": " + cudaGetErrorString(e__);  \
+      return e__ == cudaErrorMemoryAllocation ? TUCKER_ENOMEM : TUCKER_ECUDA; \
+    }                                                                       \
+  } while (0)
+
+static tucker_status read_u32(Ctx *c, const uint32_t *d, uint32_t *h, cudaStream_t s) {
+  TK_TRY(cudaMemcpyAsync(h, d, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  TK_TRY(cudaStreamSynchronize(s));
+  return TUCKER_OK;
+}
+
+tucker_status build_sorted_copies(Ctx *c, const uint32_t *coords_in, const float *vals_in, cudaStream_t s) {
+  const int N = c->N;
+  const int64_t n_in = c->nnz_in;
+  Temps tmp(c);
+  int64_t *d_dims = nullptr;
+  uint32_t *d_small = nullptr;  // [0..7] totals read back to the host
+  TK_TRY(tmp.get(&d_dims, kMaxOrder));
+  TK_TRY(tmp.get(&d_small, 8));
+  TK_TRY(cudaMemcpyAsync(d_dims, c->dims, sizeof(int64_t) * kMaxOrder, cudaMemcpyHostToDevice, s));
+  TK_TRY(cudaMemsetAsync(c->d_err, 0, sizeof(uint32_t), s));
+
+  // ---- validation
+  if (n_in > 0) {
+    validate_kernel<<<std::min<unsigned>(grid_for(n_in), (unsigned)c->num_sms * 8), 256, 0, s>>>(
+        N, n_in, coords_in, vals_in, d_dims, c->d_err);
+    TK_TRY(cudaGetLastError());
+    uint32_t err = 0;
+    tucker_status st = read_u32(c, c->d_err, &err, s);
+    if (st != TUCKER_OK) return st;
+    if (err) {
+      c->last_error = (err & kErrCoord) ? "a coordinate is >= its dimension" : "a value is not finite";
+      TK_TRY(cudaMemsetAsync(c->d_err, 0, sizeof(uint32_t), s));
+      return TUCKER_EINVAL;
+    }
+  }
+
+  // ---- scratch shared by all sorts
+  const int64_t nmax = std::max<int64_t>(n_in, 1);
+  const int64_t nb = cdiv(nmax, kRsTile);
+  int64_t maxI = 1;
+  for (int m = 0; m < N; ++m) maxI = std::max(maxI, c->dims[m]);
+  const int64_t scan_n = std::max<int64_t>(std::max<int64_t>(256 * nb, nmax), maxI + 1);
+  uint32_t *pa, *pb, *hist, *stmp, *flag, *pos;
+  TK_TRY(tmp.get(&pa, nmax));
+  TK_TRY(tmp.get(&pb, nmax));
+  TK_TRY(tmp.get(&hist, 256 * nb));
+  TK_TRY(tmp.get(&stmp, scan_tmp_elems(scan_n)));
+  TK_TRY(tmp.get(&flag, std::max<int64_t>(nmax, maxI + 1)));
+  TK_TRY(tmp.get(&pos, std::max<int64_t>(nmax, maxI + 1)));
+
+  // ---- full-key sort: LSD over modes N..1, each mode's digits low to high
+  uint32_t *perm = nullptr;
+  for (int m = N - 1; m >= 0; --m)
+    radix_sort_perm(coords_in + (int64_t)m * n_in, bits_for(c->dims[m] - 1), n_in, &perm, pa, pb, hist, stmp, s);
+  TK_TRY(cudaGetLastError());
+
+  // ---- coalesce duplicates
+  uint32_t nout = 0;
+  if (n_in > 0) {
+    mark_new_kernel<<<grid_for(n_in), 256, 0, s>>>(N, n_in, coords_in, perm, flag);
+    exclusive_scan_total(flag, pos, n_in, stmp, d_small, s);
+    tucker_status st = read_u32(c, d_small, &nout, s);
+    if (st != TUCKER_OK) return st;
+  }
+  c->nnz = nout;
+  const int64_t Z = nout;
+  TK_TRY(dev_alloc(c, &c->coords, (size_t)std::max<int64_t>(Z, 1) * N));
+  TK_TRY(dev_alloc(c, &c->vals, (size_t)std::max<int64_t>(Z, 1)));
+  double *sq = nullptr, *part = nullptr;
+  TK_TRY(tmp.get(&sq, std::max<int64_t>(Z, 1)));
+  TK_TRY(tmp.get(&part, kRedBlocks));
+  c->norm2 = 0.0;
+  if (n_in > 0) {
+    coalesce_kernel<<<grid_for(n_in), 256, 0, s>>>(N, n_in, coords_in, vals_in, perm, flag, pos, Z, c->coords, c->vals,
+                                                    sq);
+    reduce_f64_partial<<<kRedBlocks, 256, 0, s>>>(sq, Z, part);
+    reduce_f64_final<<<1, 256, 0, s>>>(part, kRedBlocks, c->norm_dev);
+    TK_TRY(cudaGetLastError());
+    TK_TRY(cudaMemcpyAsync(&c->norm2, c->norm_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+    TK_TRY(cudaStreamSynchronize(s));
+  } else {
+    TK_TRY(cudaMemsetAsync(c->norm_dev, 0, sizeof(double), s));
+  }
+
+  // ---- per-mode sorted copies
+  uint32_t *row = nullptr, *nu = nullptr, *islong = nullptr, *uoff = nullptr, *lid = nullptr;
+  TK_TRY(tmp.get(&row, std::max<int64_t>(Z, 1)));
+  TK_TRY(tmp.get(&nu, std::max<int64_t>(Z, 1) + 1));
+  TK_TRY(tmp.get(&islong, std::max<int64_t>(Z, 1) + 1));
+  TK_TRY(tmp.get(&uoff, std::max<int64_t>(Z, 1) + 1));
+  TK_TRY(tmp.get(&lid, std::max<int64_t>(Z, 1) + 1));
+  for (int n = 0; n < N; ++n) {
+    ModeCopy &mc = c->mode[n];
+    mc.I = c->dims[n];
+    mc.nother = N - 1;
+    mc.P = 1;
+    int t = 0;
+    for (int m = 0; m < N; ++m)
+      if (m != n) {
+        mc.other[t++] = m;
+        mc.P *= c->ranks[m];
+      }
+    mc.chunk = pick_chunk(Z, c->num_sms);
+    GatherArgs g{};
+    g.nother = mc.nother;
+    for (int q = 0; q < mc.nother; ++q) {
+      TK_TRY(dev_alloc(c, &mc.idx[q], (size_t)std::max<int64_t>(Z, 1)));
+      g.src[q] = c->coords + (int64_t)mc.other[q] * Z;
+      g.dst[q] = mc.idx[q];
+    }
+    TK_TRY(dev_alloc(c, &mc.val, (size_t)std::max<int64_t>(Z, 1)));
+    uint32_t *mperm = nullptr;  // mode 1: the lexicographic order is already sorted by i_1
+    if (n > 0) radix_sort_perm(c->coords + (int64_t)n * Z, bits_for(mc.I - 1), Z, &mperm, pa, pb, hist, stmp, s);
+    uint32_t S = 0;
+    if (Z > 0) {
+      gather_mode_kernel<<<grid_for(Z), 256, 0, s>>>(Z, mperm, g, c->coords + (int64_t)n * Z, row, c->vals, mc.val);
+      slice_start_kernel<<<grid_for(Z), 256, 0, s>>>(Z, row, flag);
+      exclusive_scan_total(flag, pos, Z, stmp, d_small, s);
+      tucker_status st = read_u32(c, d_small, &S, s);
+      if (st != TUCKER_OK) return st;
+    }
+    mc.S = S;
+    TK_TRY(dev_alloc(c, &mc.sptr, (size_t)S + 1));
+    TK_TRY(dev_alloc(c, &mc.sid, (size_t)std::max<uint32_t>(S, 1)));
+    uint32_t *present = nu;  // reuse: I_n + 1 <= ... not guaranteed, use dedicated buffer
+    TK_TRY(tmp.get(&present, (size_t)mc.I + 1));
+    TK_TRY(cudaMemsetAsync(present, 0, sizeof(uint32_t) * (size_t)mc.I, s));
+    if (Z > 0) {
+      slice_write_kernel<<<grid_for(Z), 256, 0, s>>>(Z, row, flag, pos, mc.sptr, mc.sid, present, S);
+    } else {
+      TK_TRY(cudaMemsetAsync(mc.sptr, 0, sizeof(uint32_t), s));
+    }
+    // empty rows
+    invert_flag_kernel<<<grid_for(mc.I), 256, 0, s>>>(mc.I, present, flag);
+    exclusive_scan_total(flag, pos, mc.I, stmp, d_small + 1, s);
+    uint32_t ne = 0;
+    tucker_status st = read_u32(c, d_small + 1, &ne, s);
+    if (st != TUCKER_OK) return st;
+    mc.n_empty = ne;
+    TK_TRY(dev_alloc(c, &mc.empty, (size_t)std::max<uint32_t>(ne, 1)));
+    if (ne) compact_kernel<<<grid_for(mc.I), 256, 0, s>>>(mc.I, flag, pos, mc.empty);
+    // work units
+    uint32_t nunits = 0, nlong = 0;
+    if (S > 0) {
+      unit_count_kernel<<<grid_for(S), 256, 0, s>>>(S, mc.sptr, (uint32_t)mc.chunk, nu, islong);
+      exclusive_scan_total(nu, uoff, S, stmp, d_small + 2, s);
+      exclusive_scan_total(islong, lid, S, stmp, d_small + 3, s);
+      uint32_t h2[2];
+      TK_TRY(cudaMemcpyAsync(h2, d_small + 2, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+      TK_TRY(cudaStreamSynchronize(s));
+      nunits = h2[0];
+      nlong = h2[1];
+    }
+    mc.n_units = nunits;
+    mc.n_long = nlong;
+    TK_TRY(dev_alloc(c, &mc.unit_e0, (size_t)std::max<uint32_t>(nunits, 1)));
+    TK_TRY(dev_alloc(c, &mc.unit_k0, (size_t)std::max<uint32_t>(nunits, 1)));
+    TK_TRY(dev_alloc(c, &mc.unit_slot, (size_t)std::max<uint32_t>(nunits, 1)));
+    TK_TRY(dev_alloc(c, &mc.long_k, (size_t)std::max<uint32_t>(nlong, 1)));
+    TK_TRY(dev_alloc(c, &mc.long_u0, (size_t)std::max<uint32_t>(nlong, 1)));
+    TK_TRY(dev_alloc(c, &mc.long_np, (size_t)std::max<uint32_t>(nlong, 1)));
+    if (S > 0)
+      unit_write_kernel<<<grid_for(S), 256, 0, s>>>(S, mc.sptr, (uint32_t)mc.chunk, nu, uoff, islong, lid, mc.unit_e0,
+                                                     mc.unit_k0, mc.unit_slot, mc.long_k, mc.long_u0, mc.long_np);
+    TK_TRY(cudaGetLastError());
+  }
+  TK_TRY(cudaStreamSynchronize(s));
+  return TUCKER_OK;
+}
+
+}  // namespace tk

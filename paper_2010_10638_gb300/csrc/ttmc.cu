@@ -1,0 +1,455 @@
+// K-b: sparse TTMc of one mode (Algorithm 2 inner loop; Section III-C):
+//     Y_(n)(i_n, :) = sum_{z in slice i_n} x_z * kron_{m != n} U_m(i_m(z), :)
+//
+// GPU design.  The remaining modes are split into a "left" group (all but the last,
+// Kronecker length PL) and the last mode (length RB), so that one nonzero contributes
+// the rank-1 block (x_z a_z) b_z^T of a PL x RB row, with a_z the Kronecker of the left
+// rows (Algorithm 4 layout: c = ra * RB + rb, last mode fastest).  One warp owns one
+// work unit of consecutive sorted nonzeros (a run of whole slices, or a piece of a long
+// slice).  Per tile of 32 nonzeros the warp
+//   1. loads indices and values coalesced (lane = position) and finds the slice of every
+//      position from 32 slice offsets with one OR-reduction (no per-nonzero row index
+//      is stored);
+//   2. gathers the factor rows with 16-byte vector loads into shared memory, scaling
+//      the left Kronecker row by x_z;
+//   3. accumulates each slice segment in registers: the warp is cut into NG groups of
+//      G lanes, each lane owns a TA x TB block of the row, the groups take alternate
+//      nonzeros and are merged by warp shuffles when the segment closes;
+//   4. writes the finished row to Y_(n) (or, for a piece of a long slice, to a partial
+//      row that a second kernel sums in piece order).
+// No global atomics: every output element has one writer, so Y is bitwise reproducible.
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace tk {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kTtmcWarps = 8;
+
+struct TtmcParams {
+  const uint32_t *idx[kMaxOrder];  // sorted coordinates of the remaining modes (ascending)
+  const void *U[kMaxOrder];        // their factors (float or bf16), row-major I_m x R_m
+  int R[kMaxOrder];                // their ranks
+  int nother;
+  const float *val;
+  const uint32_t *sptr;
+  const uint32_t *sid;
+  uint32_t S;
+  const uint32_t *unit_e0;
+  const uint32_t *unit_k0;
+  const int32_t *unit_slot;
+  int64_t n_units;
+  uint32_t Z;
+  float *Y;
+  float *carry;
+  int64_t P;
+};
+
+// Slice structure of the tile [e, e + nt) of sorted positions, kb = slice of position e.
+struct TileSlices {
+  uint32_t starts;     // bit p: a new slice starts at position p of the tile (p >= 1)
+  uint32_t kp;         // slice index of position `lane`
+  bool end_is_start;   // position e + nt starts a new slice (or is the end of all nonzeros)
+  uint32_t kb_next;    // slice of position e + nt
+};
+
+__device__ __forceinline__ TileSlices tile_slices(const uint32_t *__restrict__ sptr, uint32_t S, uint32_t kb,
+                                                  uint32_t e, int nt, int lane) {
+  const uint32_t k = kb + 1u + (uint32_t)lane;
+  const uint32_t bound = (k <= S) ? __ldg(sptr + k) : 0xffffffffu;
+  const uint32_t q = bound - e;  // >= 1: slice kb contains e
+  uint32_t starts = __reduce_or_sync(kFull, q < 32u ? (1u << q) : 0u);
+  starts &= (nt >= 32) ? kFull : ((1u << nt) - 1u);
+  TileSlices t;
+  t.starts = starts;
+  t.kp = kb + __popc(starts & ((2u << lane) - 1u));
+  t.end_is_start = __any_sync(kFull, q == (uint32_t)nt);
+  t.kb_next = kb + __popc(__ballot_sync(kFull, q <= (uint32_t)nt));
+  return t;
+}
+
+template <typename FT>
+struct Ld;
+template <>
+struct Ld<float> {
+  static __device__ __forceinline__ float4 v4(const float *row, int c) {
+    return __ldg(reinterpret_cast<const float4 *>(row + c));
+  }
+  static __device__ __forceinline__ float s(const float *row, int c) { return __ldg(row + c); }
+};
+template <>
+struct Ld<__nv_bfloat16> {
+  static __device__ __forceinline__ float4 v4(const __nv_bfloat16 *row, int c) {
+    uint2 raw = __ldg(reinterpret_cast<const uint2 *>(row + c));
+    float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&raw.x));
+    float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&raw.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+  }
+  static __device__ __forceinline__ float s(const __nv_bfloat16 *row, int c) { return __bfloat162float(row[c]); }
+};
+
+template <int T>
+__device__ __forceinline__ void lds(const float *p, float (&v)[T]) {
+  if constexpr (T % 4 == 0) {
+#pragma unroll
+    for (int i = 0; i < T; i += 4) {
+      float4 q = *reinterpret_cast<const float4 *>(p + i);
+      v[i] = q.x;
+      v[i + 1] = q.y;
+      v[i + 2] = q.z;
+      v[i + 3] = q.w;
+    }
+  } else if constexpr (T % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < T; i += 2) {
+      float2 q = *reinterpret_cast<const float2 *>(p + i);
+      v[i] = q.x;
+      v[i + 1] = q.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < T; ++i) v[i] = p[i];
+  }
+}
+
+// NL = number of left modes (0, 1 or 2); PL = product of their ranks; RB = rank of the
+// last remaining mode.  Requires RB % 4 == 0, and for NL == 2 the second left rank % 4 == 0.
+template <int NL, int PL, int RB, int TA, int TB, typename FT>
+__global__ void __launch_bounds__(kTtmcWarps * 32) ttmc_fast_kernel(const TtmcParams p) {
+  constexpr int G = (PL / TA) * (RB / TB);  // lanes per group
+  constexpr int NG = 32 / G;                // groups per warp
+  static_assert(G * NG == 32, "group size must divide the warp");
+  static_assert(RB % 4 == 0, "last rank must be a multiple of 4");
+  extern __shared__ float4 smem_f4[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float *xa = reinterpret_cast<float *>(smem_f4) + w * 32 * (PL + RB);
+  float *bb = xa + 32 * PL;
+  const int64_t u = (int64_t)blockIdx.x * kTtmcWarps + w;
+  if (u >= p.n_units) return;
+
+  const FT *UB = static_cast<const FT *>(p.U[NL]);
+  const uint32_t *idxB = p.idx[NL];
+  uint32_t e = __ldg(p.unit_e0 + u);
+  const uint32_t e_end = (u + 1 < p.n_units) ? __ldg(p.unit_e0 + u + 1) : p.Z;
+  uint32_t kb = __ldg(p.unit_k0 + u);
+  const int slot = __ldg(p.unit_slot + u);
+
+  const int g = lane / G, j = lane % G;
+  const int ra0 = (j / (RB / TB)) * TA, rb0 = (j % (RB / TB)) * TB;
+  float acc[TA][TB];
+#pragma unroll
+  for (int a = 0; a < TA; ++a)
+#pragma unroll
+    for (int b = 0; b < TB; ++b) acc[a][b] = 0.f;
+
+  while (e < e_end) {
+    const int nt = (int)min(32u, e_end - e);
+    const TileSlices ts = tile_slices(p.sptr, p.S, kb, e, nt, lane);
+
+    float x = 0.f;
+    uint32_t i0 = 0, i1 = 0, ib = 0;
+    if (lane < nt) {
+      x = __ldg(p.val + e + lane);
+      ib = __ldg(idxB + e + lane);
+      if constexpr (NL >= 1) i0 = __ldg(p.idx[0] + e + lane);
+      if constexpr (NL >= 2) i1 = __ldg(p.idx[1] + e + lane);
+    }
+    __syncwarp();
+    // ---- stage x * kron(left rows) and the last-mode rows
+    if constexpr (NL == 0) {
+      xa[lane] = x;
+    } else if constexpr (NL == 1) {
+      const FT *U0 = static_cast<const FT *>(p.U[0]);
+#pragma unroll
+      for (int it = lane; it < 32 * (PL / 4); it += 32) {
+        const int t = it / (PL / 4), c = (it % (PL / 4)) * 4;
+        const float xt = __shfl_sync(kFull, x, t);
+        const uint32_t r = __shfl_sync(kFull, i0, t);
+        float4 v = Ld<FT>::v4(U0 + (size_t)r * PL, c);
+        v.x *= xt;
+        v.y *= xt;
+        v.z *= xt;
+        v.w *= xt;
+        *reinterpret_cast<float4 *>(xa + t * PL + c) = v;
+      }
+    } else {
+      const FT *U0 = static_cast<const FT *>(p.U[0]);
+      const FT *U1 = static_cast<const FT *>(p.U[1]);
+      const int R1 = p.R[1], R0 = p.R[0];
+#pragma unroll 4
+      for (int it = lane; it < 32 * (PL / 4); it += 32) {
+        const int t = it / (PL / 4), c = (it % (PL / 4)) * 4;
+        const float xt = __shfl_sync(kFull, x, t);
+        const uint32_t r0 = __shfl_sync(kFull, i0, t);
+        const uint32_t r1 = __shfl_sync(kFull, i1, t);
+        const int a0 = c / R1, a1 = c - a0 * R1;
+        const float s0 = xt * Ld<FT>::s(U0 + (size_t)r0 * R0, a0);
+        float4 v = Ld<FT>::v4(U1 + (size_t)r1 * R1, a1);
+        v.x *= s0;
+        v.y *= s0;
+        v.z *= s0;
+        v.w *= s0;
+        *reinterpret_cast<float4 *>(xa + t * PL + c) = v;
+      }
+    }
+#pragma unroll
+    for (int it = lane; it < 32 * (RB / 4); it += 32) {
+      const int t = it / (RB / 4), c = (it % (RB / 4)) * 4;
+      const uint32_t r = __shfl_sync(kFull, ib, t);
+      *reinterpret_cast<float4 *>(bb + t * RB + c) = Ld<FT>::v4(UB + (size_t)r * RB, c);
+    }
+    __syncwarp();
+
+    // ---- segments of equal slice inside the tile
+    uint32_t segs = ts.starts | 1u;
+    while (segs) {
+      const int p0 = __ffs(segs) - 1;
+      segs &= segs - 1u;
+      const int p1 = segs ? (__ffs(segs) - 1) : nt;
+      int q = p0 + g;
+      auto step = [&](int qq) {
+        float av[TA], bv[TB];
+        lds<TA>(xa + qq * PL + ra0, av);
+        lds<TB>(bb + qq * RB + rb0, bv);
+#pragma unroll
+        for (int a = 0; a < TA; ++a)
+#pragma unroll
+          for (int b = 0; b < TB; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+      };
+      for (; q + NG < p1; q += 2 * NG) {
+        step(q);
+        step(q + NG);
+      }
+      if (q < p1) step(q);
+      const bool flush = (p1 < nt) || ts.end_is_start || (e + (uint32_t)nt == e_end);
+      if (flush) {
+#pragma unroll
+        for (int o = G; o < 32; o <<= 1)
+#pragma unroll
+          for (int a = 0; a < TA; ++a)
+#pragma unroll
+            for (int b = 0; b < TB; ++b) acc[a][b] += __shfl_xor_sync(kFull, acc[a][b], o);
+        const uint32_t kseg = __shfl_sync(kFull, ts.kp, p0);
+        if (g == 0) {
+          float *dst = (slot >= 0) ? p.carry + (size_t)slot * p.P : p.Y + (size_t)__ldg(p.sid + kseg) * p.P;
+#pragma unroll
+          for (int a = 0; a < TA; ++a) {
+            float *d = dst + (size_t)(ra0 + a) * RB + rb0;
+            if constexpr (TB % 4 == 0) {
+#pragma unroll
+              for (int b = 0; b < TB; b += 4)
+                *reinterpret_cast<float4 *>(d + b) = make_float4(acc[a][b], acc[a][b + 1], acc[a][b + 2], acc[a][b + 3]);
+            } else {
+#pragma unroll
+              for (int b = 0; b < TB; ++b) d[b] = acc[a][b];
+            }
+          }
+        }
+#pragma unroll
+        for (int a = 0; a < TA; ++a)
+#pragma unroll
+          for (int b = 0; b < TB; ++b) acc[a][b] = 0.f;
+      }
+    }
+    kb = ts.kb_next;
+    e += (uint32_t)nt;
+    __syncwarp();
+  }
+}
+
+// Any shape: each lane owns CPL columns of a block of 32*CPL columns (grid.y), and
+// forms its Kronecker entries directly from the factor rows (cached loads).
+template <int CPL, typename FT>
+__global__ void __launch_bounds__(kTtmcWarps * 32) ttmc_generic_kernel(const TtmcParams p) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t u = (int64_t)blockIdx.x * kTtmcWarps + w;
+  if (u >= p.n_units) return;
+  const int nother = p.nother;
+  // column decode
+  int rr[CPL][kMaxOrder];
+  bool own[CPL];
+  int64_t col[CPL];
+#pragma unroll
+  for (int s = 0; s < CPL; ++s) {
+    col[s] = (int64_t)blockIdx.y * 32 * CPL + lane + 32 * s;
+    own[s] = col[s] < p.P;
+    int64_t cc = own[s] ? col[s] : 0;
+    for (int t = kMaxOrder - 1; t >= 0; --t) {
+      if (t < nother) {
+        rr[s][t] = (int)(cc % p.R[t]);
+        cc /= p.R[t];
+      } else {
+        rr[s][t] = 0;
+      }
+    }
+  }
+  uint32_t e = __ldg(p.unit_e0 + u);
+  const uint32_t e_end = (u + 1 < p.n_units) ? __ldg(p.unit_e0 + u + 1) : p.Z;
+  uint32_t kb = __ldg(p.unit_k0 + u);
+  const int slot = __ldg(p.unit_slot + u);
+  float acc[CPL];
+#pragma unroll
+  for (int s = 0; s < CPL; ++s) acc[s] = 0.f;
+  while (e < e_end) {
+    const int nt = (int)min(32u, e_end - e);
+    const TileSlices ts = tile_slices(p.sptr, p.S, kb, e, nt, lane);
+    float x = 0.f;
+    uint32_t id[kMaxOrder];
+#pragma unroll
+    for (int t = 0; t < kMaxOrder; ++t) id[t] = 0;
+    if (lane < nt) {
+      x = __ldg(p.val + e + lane);
+      for (int t = 0; t < nother; ++t) id[t] = __ldg(p.idx[t] + e + lane);
+    }
+    uint32_t segs = ts.starts | 1u;
+    while (segs) {
+      const int p0 = __ffs(segs) - 1;
+      segs &= segs - 1u;
+      const int p1 = segs ? (__ffs(segs) - 1) : nt;
+      for (int q = p0; q < p1; ++q) {
+        const float xq = __shfl_sync(kFull, x, q);
+        uint32_t iq[kMaxOrder];
+#pragma unroll
+        for (int t = 0; t < kMaxOrder; ++t) iq[t] = __shfl_sync(kFull, id[t], q);
+#pragma unroll
+        for (int s = 0; s < CPL; ++s) {
+          float v = xq;
+          for (int t = 0; t < nother; ++t)
+            v *= Ld<FT>::s(static_cast<const FT *>(p.U[t]) + (size_t)iq[t] * p.R[t], rr[s][t]);
+          acc[s] += v;
+        }
+      }
+      const bool flush = (p1 < nt) || ts.end_is_start || (e + (uint32_t)nt == e_end);
+      if (flush) {
+        const uint32_t kseg = __shfl_sync(kFull, ts.kp, p0);
+        float *dst = (slot >= 0) ? p.carry + (size_t)slot * p.P : p.Y + (size_t)__ldg(p.sid + kseg) * p.P;
+#pragma unroll
+        for (int s = 0; s < CPL; ++s) {
+          if (own[s]) dst[col[s]] = acc[s];
+          acc[s] = 0.f;
+        }
+      }
+    }
+    kb = ts.kb_next;
+    e += (uint32_t)nt;
+  }
+}
+
+// Rows of slices split over several units: sum the partial rows in unit order.
+__global__ void ttmc_fixup_kernel(const uint32_t *long_k, const uint32_t *long_u0, const uint32_t *long_np,
+                                  const uint32_t *sid, const float *carry, float *Y, int64_t P) {
+  const int64_t l = blockIdx.x;
+  const uint32_t row = sid[long_k[l]], u0 = long_u0[l], np = long_np[l];
+  for (int64_t c = threadIdx.x; c < P; c += blockDim.x) {
+    float s = 0.f;
+    for (uint32_t q = 0; q < np; ++q) s += carry[(size_t)(u0 + q) * P + c];
+    Y[(size_t)row * P + c] = s;
+  }
+}
+
+__global__ void ttmc_zero_rows_kernel(const uint32_t *rows, int64_t n, float *Y, int64_t P) {
+  for (int64_t r = blockIdx.x; r < n; r += gridDim.x) {
+    float *y = Y + (size_t)rows[r] * P;
+    for (int64_t c = threadIdx.x; c < P; c += blockDim.x) y[c] = 0.f;
+  }
+}
+
+template <int NL, int PL, int RB, int TA, int TB, typename FT>
+static cudaError_t run_fast(const TtmcParams &p, cudaStream_t s) {
+  const size_t smem = (size_t)kTtmcWarps * 32 * (PL + RB) * sizeof(float);
+  auto kern = ttmc_fast_kernel<NL, PL, RB, TA, TB, FT>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  const unsigned blocks = (unsigned)((p.n_units + kTtmcWarps - 1) / kTtmcWarps);
+  kern<<<blocks, kTtmcWarps * 32, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <typename FT>
+static cudaError_t run_generic(const TtmcParams &p, cudaStream_t s) {
+  constexpr int CPL = 4;
+  const unsigned blocks = (unsigned)((p.n_units + kTtmcWarps - 1) / kTtmcWarps);
+  const unsigned cols = (unsigned)((p.P + 32 * CPL - 1) / (32 * CPL));
+  ttmc_generic_kernel<CPL, FT><<<dim3(blocks, cols), kTtmcWarps * 32, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+// Shape dispatch.  Returns false when no specialised kernel covers the shape.
+template <typename FT>
+static bool dispatch_fast(const TtmcParams &p, cudaStream_t s, cudaError_t *err) {
+  const int no = p.nother;
+  const int RB = p.R[no - 1];
+#define TK_FAST(NL_, PL_, RB_, TA_, TB_)                   \
+  {                                                        \
+    *err = run_fast<NL_, PL_, RB_, TA_, TB_, FT>(p, s);    \
+    return true;                                           \
+  }
+  if (no == 1) {
+    if (RB == 16) TK_FAST(0, 1, 16, 1, 4)
+    if (RB == 32) TK_FAST(0, 1, 32, 1, 4)
+    if (RB == 8) TK_FAST(0, 1, 8, 1, 4)
+  } else if (no == 2) {
+    const int PL = p.R[0];
+    if (PL == 16 && RB == 16) TK_FAST(1, 16, 16, 4, 4)
+    if (PL == 8 && RB == 8) TK_FAST(1, 8, 8, 2, 4)
+    if (PL == 32 && RB == 32) TK_FAST(1, 32, 32, 8, 4)
+    if (PL == 16 && RB == 8) TK_FAST(1, 16, 8, 4, 4)
+    if (PL == 8 && RB == 16) TK_FAST(1, 8, 16, 4, 4)
+  } else if (no == 3) {
+    const int PL = p.R[0] * p.R[1];
+    if (p.R[1] % 4 == 0) {
+      if (PL == 64 && RB == 8) TK_FAST(2, 64, 8, 4, 4)
+      if (PL == 64 && RB == 16) TK_FAST(2, 64, 16, 8, 4)
+      if (PL == 16 && RB == 4) TK_FAST(2, 16, 4, 2, 4)
+    }
+  }
+#undef TK_FAST
+  return false;
+}
+
+tucker_status launch_ttmc(Ctx *c, int mode, float *Y, cudaStream_t s) {
+  const ModeCopy &mc = c->mode[mode];
+  const bool bf16 = (c->flags & TUCKER_F_BF16_FACTORS) != 0;
+  TtmcParams p{};
+  p.nother = mc.nother;
+  for (int t = 0; t < mc.nother; ++t) {
+    const int m = mc.other[t];
+    p.idx[t] = mc.idx[t];
+    p.U[t] = bf16 ? static_cast<const void *>(c->U16[m]) : static_cast<const void *>(c->U32[m]);
+    p.R[t] = c->ranks[m];
+  }
+  p.val = mc.val;
+  p.sptr = mc.sptr;
+  p.sid = mc.sid;
+  p.S = (uint32_t)mc.S;
+  p.unit_e0 = mc.unit_e0;
+  p.unit_k0 = mc.unit_k0;
+  p.unit_slot = mc.unit_slot;
+  p.n_units = mc.n_units;
+  p.Z = (uint32_t)c->nnz;
+  p.Y = Y;
+  p.carry = c->carry;
+  p.P = mc.P;
+  if (mc.n_units > 0) {
+    cudaError_t err = cudaSuccess;
+    bool done = bf16 ? dispatch_fast<__nv_bfloat16>(p, s, &err) : dispatch_fast<float>(p, s, &err);
+    if (!done) err = bf16 ? run_generic<__nv_bfloat16>(p, s) : run_generic<float>(p, s);
+    TK_CUDA(err);
+  }
+  if (mc.n_long > 0) {
+    ttmc_fixup_kernel<<<(unsigned)mc.n_long, 256, 0, s>>>(mc.long_k, mc.long_u0, mc.long_np, mc.sid, c->carry, Y,
+                                                          mc.P);
+    TK_CUDA(cudaGetLastError());
+  }
+  if (mc.n_empty > 0) {
+    ttmc_zero_rows_kernel<<<(unsigned)std::min<int64_t>(mc.n_empty, 65535), 256, 0, s>>>(mc.empty, mc.n_empty, Y,
+                                                                                        mc.P);
+    TK_CUDA(cudaGetLastError());
+  }
+  return TUCKER_OK;
+}
+
+}  // namespace tk

@@ -1,0 +1,80 @@
+"""GPU parity of the FP64 QR with column pivoting (K-c) against the oracle.
+
+Pivots must be identical wherever the top two trailing column norms are separated
+by a relative gap > 1e-10 (the GPU downdates norms, the oracle recomputes them);
+Q and diag(R) then agree to 1e-12 (same sign convention: v = a + sign(a_1)||a|| e_1)."""
+import numpy as np
+import pytest
+
+import oracle
+from tests.gpu_util import lib, torch
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_qrp(A, k):
+    T = lib()
+    Q, piv, rd = T.qrp_leading(torch.as_tensor(A).cuda(), k)
+    return Q.cpu().numpy(), piv.cpu().numpy(), rd.cpu().numpy()
+
+
+def min_pivot_gap(A, k):
+    """Smallest relative gap between the best and second-best trailing norm over the
+    first k pivot decisions of exact-norm QRP (computed with the oracle's reflectors)."""
+    res = oracle.qrp(A, k)
+    W = A[:, res.piv].copy()
+    gaps = []
+    rest = [c for c in range(A.shape[1]) if c not in set(res.piv.tolist())]
+    cols = np.concatenate([res.piv, rest]).astype(int)
+    W = A[:, cols]
+    Q = res.Q
+    for j in range(k):
+        R = W - Q[:, :j] @ (Q[:, :j].T @ W)
+        nrm = np.sort(np.linalg.norm(R[:, j:], axis=0))[::-1]
+        if len(nrm) > 1 and nrm[0] > 0:
+            gaps.append((nrm[0] - nrm[1]) / nrm[0])
+    return min(gaps) if gaps else 1.0
+
+
+@pytest.mark.parametrize("m,n,k", [(500, 64, 16), (3000, 256, 16), (64, 64, 64), (257, 33, 8), (40, 300, 20),
+                                   (1, 5, 1), (6, 1, 1)])
+def test_qrp_matches_oracle(m, n, k):
+    rng = np.random.default_rng(m * 1000 + n + k)
+    A = rng.standard_normal((m, n)) * rng.uniform(0.2, 5.0, n)
+    Q, piv, rd = gpu_qrp(A, k)
+    ref = oracle.qrp(A, k)
+    assert min_pivot_gap(A, k) > 1e-10
+    np.testing.assert_array_equal(piv, ref.piv)
+    np.testing.assert_allclose(rd, ref.rdiag, rtol=1e-11, atol=1e-12 * abs(ref.rdiag[0]))
+    np.testing.assert_allclose(Q, ref.Q, atol=1e-11)
+    np.testing.assert_allclose(Q.T @ Q, np.eye(k), atol=1e-13)
+
+
+def test_qrp_rank_deficient_and_zero_columns():
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((200, 3)) @ rng.standard_normal((3, 40))
+    A[:, 5] = 0.0
+    Q, piv, rd = gpu_qrp(A, 6)
+    assert np.all(np.isfinite(Q)) and np.all(np.isfinite(rd))
+    np.testing.assert_allclose(Q.T @ Q, np.eye(6), atol=1e-12)
+    assert np.all(np.abs(rd[3:]) < 1e-10 * abs(rd[0]))
+    ref = oracle.qrp(A, 3)
+    np.testing.assert_array_equal(piv[:3], ref.piv)
+    # the leading 3 columns span the column space
+    np.testing.assert_allclose(Q[:, :3] @ (Q[:, :3].T @ A), A, atol=1e-9 * np.abs(A).max())
+
+
+def test_qrp_all_zero_matrix():
+    Q, piv, rd = gpu_qrp(np.zeros((30, 7)), 4)
+    np.testing.assert_array_equal(rd, 0.0)
+    np.testing.assert_allclose(Q, np.eye(30)[:, :4], atol=0)
+    np.testing.assert_array_equal(piv, [0, 1, 2, 3])
+
+
+def test_qrp_rejects_bad_sizes():
+    T = lib()
+    with pytest.raises(T.TuckerError):
+        T.qrp_leading(torch.zeros((3, 5), dtype=torch.float64, device="cuda"), 4)
+    with pytest.raises(T.TuckerError):
+        T.qrp_leading(torch.zeros((3, 5), dtype=torch.float64, device="cuda"), 2,
+                      work=torch.empty(64, dtype=torch.uint8, device="cuda"))
