@@ -1,0 +1,442 @@
+"""Benchmark of the sparse Tucker (HOOI) hot path on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload skew-20M]
+
+A step is one HOOI sweep (Algorithm 2): TTMc + QRP for every mode, then the core
+tensor and the fit, on a seeded synthetic tensor resident in HBM.  The metric is
+nonzeros processed per second per mode: value = N_modes * nnz / (time of one sweep),
+whole job over all ranks.  Each rank runs an independent replica (weak scaling;
+the method has no exchange step between independent decompositions).
+
+Besides the JSON line's required keys it reports the per-phase split of a sweep,
+TTMc nonzeros/s per mode, the roofline of the dominant kernel, the BF16-factor form,
+the one-off initialisation, the end-to-end rate through the C ABI from pinned host
+buffers, and the FP64 oracle timed on the host cores on a bounded sample.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sparse TTMc nonzeros/sec per mode and HOOI iteration time (s), % of HBM roofline"
+UNIT = "nonzeros/s per mode (N_modes * nnz / HOOI sweep time)"
+SM_COUNT, SM_MAX_MHZ, FP32_LANES = 152, 2070.0, 128
+FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12  # 80.5, from unit counts and max clock
+FP64_PEAK_TFLOPS_NOMINAL = 1.25
+L2_BYTES = 129 * 1024 * 1024
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.15)
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.1)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- helpers
+def file_sha(path):
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def profile_traffic(kernel_tag: str):
+    """Per-launch DRAM bytes from a committed ncu summary, if it was taken on the current source."""
+    p = os.path.join(ROOT, "profiles", f"{kernel_tag}.md")
+    if not os.path.exists(p):
+        return None
+    vals = {}
+    with open(p) as f:
+        for line in f:
+            if ":" in line and line.strip().startswith("- "):
+                k, v = line.strip()[2:].split(":", 1)
+                vals[k.strip()] = v.strip()
+    src = os.path.join(ROOT, "paper_2010_10638_gb300", "csrc", vals.get("source", "ttmc.cu"))
+    if "source_sha" not in vals or not os.path.exists(src) or file_sha(src) != vals["source_sha"]:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def oracle_sample(inst, sample_nnz):
+    """The oracle on a bounded sample: one HOOI sweep over the first `sample_nnz` listed
+    entries of the same workload (same dims, ranks, initial factors).  Returns (seconds, nnz)."""
+    import oracle
+    w = inst.workload
+    coords = np.ascontiguousarray(inst.coords[:, :sample_nnz])
+    vals = inst.vals[:sample_nnz].astype(np.float64)
+    cc, cv = oracle.coalesce(coords, vals)
+    t0 = time.perf_counter()
+    oracle.hooi(w.dims, w.ranks, cc, cv, inst.U0, 1, coalesced=True)
+    return time.perf_counter() - t0, cc.shape[1]
+
+
+def dist_setup(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank, world, _ = dist_setup(args.gpus)
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2010_10638_gb300 import synth
+    oracle.build()
+    inst = synth.make(args.workload)
+    w = inst.workload
+    N = len(w.dims)
+    steps = max(1, min(args.steps, 5))
+    warm = min(args.warmup, 1)
+    sample = args.oracle_nnz
+    for _ in range(warm):
+        oracle_sample(inst, sample)
+    times, nz = [], 0
+    for _ in range(steps):
+        t, nz = oracle_sample(inst, sample)
+        times.append(t)
+    tstep = sum(times) / len(times)
+    value = N * nz / tstep
+    desc = (f"one oracle HOOI sweep (C, FP64, single thread) over the first {sample:,} listed entries of "
+            f"{w.name} ({nz:,} after coalescing), same dims/ranks/initial factors; {steps} timed of "
+            f"{args.steps} requested steps")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": steps,
+            "warmup": warm, "ms_per_step": tstep * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "dims": list(w.dims), "nnz": w.nnz, "ranks": list(w.ranks)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_mine(args):
+    import torch
+    rank, world, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2010_10638_gb300 import build as libbuild
+    from paper_2010_10638_gb300 import synth, tucker as T
+    if rank == 0 or world == 1:
+        libbuild.build()
+    if world > 1:
+        torch.distributed.barrier()
+    T.load()
+
+    inst = synth.make(args.workload)
+    w = inst.workload
+    N, Z = len(w.dims), w.nnz
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        coords_d = torch.as_tensor(inst.coords.astype(np.int32)).to(dev)
+        vals_d = torch.as_tensor(inst.vals).to(dev)
+        U0_d = [torch.as_tensor(u).to(dev) for u in inst.U0]
+        torch.cuda.synchronize()
+        # one-off initialisation (a1), timed separately
+        t0 = time.perf_counter()
+        ctx = T.tucker_init(w.dims, coords_d, vals_d, w.ranks, U0_d, fit_device=True, stream=stream)
+        torch.cuda.synchronize()
+        init_s = time.perf_counter() - t0
+        Zc = T.tucker_nnz(ctx)
+        fit_buf = torch.zeros(1, dtype=torch.float64, device=dev)
+        flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+        for _ in range(args.warmup):
+            T.hooi_iter(ctx, fit_buf, stream=stream)
+        torch.cuda.synchronize()
+
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        launches0 = T.tucker_kernel_launches()
+        with ClockSampler(local) as clk:
+            for i in range(args.steps):
+                flush.fill_(float(i))  # evict L2 between timed steps (outside the events)
+                starts[i].record(stream)
+                T.hooi_iter(ctx, fit_buf, stream=stream)
+                ends[i].record(stream)
+            torch.cuda.synchronize()
+        launches = T.tucker_kernel_launches() - launches0
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+        ms_per_step = sum(step_ms) / len(step_ms)
+        fit = float(fit_buf.item())
+
+        # max over ranks
+        if world > 1:
+            t = torch.tensor([ms_per_step], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms_per_step = float(t.item())
+
+        # per-phase split of a sweep (profiling pass, events inside the library)
+        T.tucker_set_profiling(ctx, True)
+        phase = []
+        for _ in range(5):
+            flush.fill_(0.0)
+            T.hooi_iter(ctx, fit_buf, stream=stream)
+            phase.append(T.tucker_phase_times(ctx))
+        T.tucker_set_profiling(ctx, False)
+        phase_ms = [statistics.median(p[i] for p in phase) for i in range(2 * N + 1)]
+
+        # TTMc alone, per mode: launch durations with events on the launching stream
+        ttmc_ms = []
+        for n in range(N):
+            Y = torch.empty((w.dims[n], ctx.P(n)), dtype=torch.float32, device=dev)
+            T.ttmc_mode(ctx, n, Y, stream=stream)
+            evs = []
+            for i in range(10):
+                flush.fill_(float(i))
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                T.ttmc_mode(ctx, n, Y, stream=stream)
+                b.record(stream)
+                evs.append((a, b))
+            torch.cuda.synchronize()
+            ttmc_ms.append(statistics.median(a.elapsed_time(b) for a, b in evs))
+            del Y
+
+        # BF16-factor form on the same workload
+        bf16 = None
+        if not args.no_bf16:
+            ctxb = T.tucker_init(w.dims, coords_d, vals_d, w.ranks, U0_d, bf16=True, fit_device=True, stream=stream)
+            bms = []
+            for n in range(N):
+                Y = torch.empty((w.dims[n], ctxb.P(n)), dtype=torch.float32, device=dev)
+                T.ttmc_mode(ctxb, n, Y, stream=stream)
+                evs = []
+                for i in range(10):
+                    flush.fill_(float(i))
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    T.ttmc_mode(ctxb, n, Y, stream=stream)
+                    b.record(stream)
+                    evs.append((a, b))
+                torch.cuda.synchronize()
+                bms.append(statistics.median(a.elapsed_time(b) for a, b in evs))
+            for _ in range(2):
+                T.hooi_iter(ctxb, fit_buf, stream=stream)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(5):
+                T.hooi_iter(ctxb, fit_buf, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            sweep_b = e0.elapsed_time(e1) / 5
+            bf16 = {"ttmc_ms_per_mode": bms, "ttmc_nnz_per_s_per_mode": [Zc / (t * 1e-3) for t in bms],
+                    "hooi_s_per_iter": sweep_b * 1e-3, "value": N * Zc / (sweep_b * 1e-3)}
+            T.tucker_free(ctxb)
+
+    # ---- end to end through the C ABI from pinned host buffers: the whole decomposition
+    # job of the workload (init + its sweeps + read back fit, core and factors)
+    e2e = None
+    if not args.no_e2e:
+        import torch as _t
+        coords_h = _t.from_numpy(inst.coords.astype(np.uint32).view(np.int32)).pin_memory()
+        vals_h = _t.from_numpy(inst.vals).pin_memory()
+        U0_h = _t.from_numpy(np.concatenate([u.reshape(-1) for u in inst.U0])).pin_memory()
+        Uh = [_t.empty((w.dims[n], w.ranks[n]), dtype=_t.float64).pin_memory() for n in range(N)]
+        Gh = _t.empty(w.ranks, dtype=_t.float64).pin_memory()
+        h2d = coords_h.numel() * 4 + vals_h.numel() * 4 + U0_h.numel() * 8
+        d2h = 8 + Gh.numel() * 8 + sum(u.numel() * 8 for u in Uh)
+        lib = T.load()
+        import ctypes
+        dims_a = (ctypes.c_int64 * N)(*w.dims)
+        ranks_a = (ctypes.c_int * N)(*w.ranks)
+        ts = []
+        for rep in range(1 + max(1, min(args.steps, 3))):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h = ctypes.c_void_p()
+            rc = lib.tucker_init(ctypes.byref(h), N, dims_a, Z, coords_h.data_ptr(), vals_h.data_ptr(), ranks_a,
+                                 U0_h.data_ptr(), 0, T.TUCKER_F_HOST_INPUT, _stream(stream))
+            assert rc == 0, rc
+            f = ctypes.c_double()
+            for _ in range(w.iters - 1):
+                assert lib.hooi_iter(h, None, _stream(stream)) == 0
+            assert lib.hooi_iter(h, ctypes.addressof(f), _stream(stream)) == 0
+            with torch.cuda.stream(stream):
+                Gd = torch.empty(w.ranks, dtype=torch.float64, device=dev)
+                assert lib.core_tensor(h, Gd.data_ptr(), _stream(stream)) == 0
+                Gh.copy_(Gd, non_blocking=True)
+                for n in range(N):
+                    Ud = torch.empty((w.dims[n], w.ranks[n]), dtype=torch.float64, device=dev)
+                    assert lib.tucker_get_factor(h, n, Ud.data_ptr(), _stream(stream)) == 0
+                    Uh[n].copy_(Ud, non_blocking=True)
+            stream.synchronize()
+            t1 = time.perf_counter()
+            lib.tucker_free(h)
+            if rep > 0:
+                ts.append(t1 - t0)
+        tj = statistics.median(ts)
+        e2e = {"value": N * Zc * w.iters / tj, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "job_s": tj,
+               "step": f"tucker_init from pinned host COO + {w.iters} hooi_iter + fit/core/factors read back"}
+
+    # ---- roofline of the dominant kernel
+    hbm_peak, hbm_src = peaks()
+    ttmc_total = sum(phase_ms[2 * n] for n in range(N))
+    qrp_total = sum(phase_ms[2 * n + 1] for n in range(N))
+    flops = [2.0 * ctx.P(n) * Zc for n in range(N)]
+    bytes_alg = [4.0 * N * Zc + 4.0 * w.dims[n] * ctx.P(n) + 4.0 * (w.dims[n] + 1) for n in range(N)]
+    ttmc_avg_ms = sum(ttmc_ms) / N
+    ttmc_flops = sum(flops) / N
+    ttmc_bytes = sum(bytes_alg) / N
+    ttmc_roof = {"kernel": "ttmc_fast_kernel<1,16,16,4,4,float> (+ fixup)", "bound": "alu",
+                 "achieved": ttmc_flops / (ttmc_avg_ms * 1e-3) / 1e12, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                 "frac": ttmc_flops / (ttmc_avg_ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
+                 "traffic": profile_traffic("ttmc_skew-20M"),
+                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                 "hbm_view": {"achieved_gbs": ttmc_bytes / (ttmc_avg_ms * 1e-3) / 1e9, "peak_gbs": hbm_peak,
+                              "frac": ttmc_bytes / (ttmc_avg_ms * 1e-3) / 1e9 / hbm_peak,
+                              "peak_source": hbm_src, "alg_bytes_per_launch": ttmc_bytes},
+                 "alg_flops_per_launch": ttmc_flops, "avg_launch_ms": ttmc_avg_ms}
+    # QRP: k sweeps of 2*m*n FP64 flops over Y_(n) (tall modes) dominate its arithmetic
+    qflops = 0.0
+    for n in range(N):
+        m_, n_ = w.dims[n], ctx.P(n)
+        if n_ > m_:
+            qflops += 2.0 * m_ * m_ * n_ + 2.0 * w.ranks[n] * m_ * m_
+        else:
+            qflops += 2.0 * w.ranks[n] * m_ * n_
+    qrp_roof = {"kernel": "qrp_* (FP64 Householder QRP, all modes)", "bound": "alu",
+                "achieved": qflops / (qrp_total * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS_NOMINAL, "unit": "TFLOP/s",
+                "frac": qflops / (qrp_total * 1e-3) / 1e12 / FP64_PEAK_TFLOPS_NOMINAL, "traffic": None,
+                "peak_source": "nominal FP64 1.25 TFLOP/s"}
+    dominant = ttmc_roof if ttmc_total >= qrp_total else qrp_roof
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        t, nz = oracle_sample(inst, args.oracle_nnz)
+        cpu = {"value": N * nz / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one oracle HOOI sweep (C, FP64, single thread) over the first {args.oracle_nnz:,} listed "
+                         f"entries of {w.name} ({nz:,} after coalescing); {t:.1f} s"}
+
+    clocks = clk.summary()
+    value = world * N * Zc / (ms_per_step * 1e-3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "dims": list(w.dims), "nnz": w.nnz, "nnz_coalesced": Zc,
+                       "ranks": list(w.ranks), "l2": "flushed between timed steps (256 MiB write)",
+                       "precision": "TTMc FP32, QRP/core/fit FP64", "replicas": world},
+            "hooi_s_per_iter": ms_per_step * 1e-3,
+            "phases_ms": {"ttmc": [phase_ms[2 * n] for n in range(N)], "qrp": [phase_ms[2 * n + 1] for n in range(N)],
+                          "core_fit": phase_ms[2 * N]},
+            "ttmc_nnz_per_s_per_mode": [Zc / (t * 1e-3) for t in ttmc_ms],
+            "roofline": dominant, "roofline_other": qrp_roof if dominant is ttmc_roof else ttmc_roof,
+            "init_s": init_s, "fit_after_warmup_and_steps": fit,
+            "bf16_factor_form": bf16, "e2e": e2e, "cpu_baseline": cpu,
+            "clocks": clocks, "gpu_launches": int(launches)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    T.tucker_free(ctx)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def _stream(s):
+    return int(s.cuda_stream)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--workload", default="skew-20M")
+    ap.add_argument("--oracle-nnz", type=int, default=1_000_000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-bf16", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "mine":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_mine(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

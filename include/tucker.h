@@ -169,6 +169,19 @@ TUCKER_API tucker_status tucker_sync_status(tucker_ctx *c, void *stream);
  * Synchronises the context's internal work first. */
 TUCKER_API void tucker_free(tucker_ctx *c);
 
+/*
+ * Instrumentation (no counterpart in the paper; used to report where a sweep spends
+ * its time).  With profiling on, hooi_iter records CUDA events on its stream around
+ * each phase; tucker_phase_times waits for the last event of the latest sweep and
+ * writes 2N+1 durations in milliseconds: TTMc of mode 1, QRP (and factor copy) of
+ * mode 1, ..., TTMc of mode N, QRP of mode N, core tensor + fit.  Returns the number
+ * written, or -1 (profiling off, no complete sweep recorded, cap too small).
+ */
+TUCKER_API tucker_status tucker_set_profiling(tucker_ctx *c, int enable);
+TUCKER_API int tucker_phase_times(tucker_ctx *c, float *ms, int cap);
+/* Number of kernels libtucker has launched in this process, over all contexts. */
+TUCKER_API uint64_t tucker_kernel_launches(void);
+
 TUCKER_API const char *tucker_status_str(tucker_status s);
 /* Text of the last error recorded on this context ("" if none); valid until the next call. */
 TUCKER_API const char *tucker_last_error(const tucker_ctx *c);

@@ -3,6 +3,7 @@
 // kernels of reorder.cu (K-a), ttmc.cu (K-b), qrp.cu (K-c), core.cu (K-d) and
 // adjoint.cu (K-e).
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <new>
 
@@ -16,6 +17,9 @@ struct tucker_ctx {
 
 namespace tk {
 
+static std::atomic<uint64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
 __global__ void f64_to_f32_kernel(const double *in, int64_t n, float *out32, __nv_bfloat16 *out16) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double v = in[i];
@@ -28,6 +32,7 @@ void refresh_factor_copies(Ctx *c, int m, cudaStream_t s) {
   const int64_t n = c->dims[m] * c->ranks[m];
   const unsigned b = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4096));
   f64_to_f32_kernel<<<b, 256, 0, s>>>(c->U64[m], n, c->U32[m], c->U16[m]);
+  ::tk::count_launch();
 }
 
 // SplitMix64 (Steele, Lea, Flood 2014) as a counter-based generator; Box-Muller for N(0,1).
@@ -153,6 +158,7 @@ static tucker_status init_impl(Ctx *c, const uint32_t *coords, const float *vals
     for (int m = 0; m < N; ++m) {
       const int64_t n = c->dims[m] * c->ranks[m];
       gaussian_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(seed, m, n, g);
+      ::tk::count_launch();
       QrpWork w;
       qrp_bind_work(&w, c->qw.V, c->dims[m], c->ranks[m], c->ranks[m], c->num_sms);
       st = qrp_run_f64(g, c->dims[m], c->ranks[m], c->ranks[m], c->ranks[m], c->U64[m], c->ranks[m], nullptr,
@@ -169,11 +175,22 @@ static tucker_status init_impl(Ctx *c, const uint32_t *coords, const float *vals
   return TUCKER_OK;
 }
 
+static tucker_status mark(Ctx *c, int i, cudaStream_t s) {
+  if (!c->profiling) return TUCKER_OK;
+  if (!c->ev[i]) TK_CUDA(cudaEventCreate(&c->ev[i]));
+  TK_CUDA(cudaEventRecord(c->ev[i], s));
+  c->n_ev = i + 1;
+  return TUCKER_OK;
+}
+
 static tucker_status hooi_impl(Ctx *c, double *fit_out, cudaStream_t s) {
   const int N = c->N;
+  tucker_status st = mark(c, 0, s);
+  if (st != TUCKER_OK) return st;
   for (int n = 0; n < N; ++n) {
     const ModeCopy &mc = c->mode[n];
-    tucker_status st = launch_ttmc(c, n, c->Y, s);
+    st = launch_ttmc(c, n, c->Y, s);
+    if (st == TUCKER_OK) st = mark(c, 2 * n + 1, s);
     if (st != TUCKER_OK) return st;
     const int k = c->ranks[n];
     const int ncols = qrp_n_cols(c, n);
@@ -187,9 +204,13 @@ static tucker_status hooi_impl(Ctx *c, double *fit_out, cudaStream_t s) {
     }
     if (st != TUCKER_OK) return st;
     refresh_factor_copies(c, n, s);
+    st = mark(c, 2 * n + 2, s);
+    if (st != TUCKER_OK) return st;
   }
   launch_core(c, c->Y, c->U64[N - 1], c->G, s);
   TK_CUDA(cudaGetLastError());
+  st = mark(c, 2 * N + 1, s);
+  if (st != TUCKER_OK) return st;
   c->G_valid = true;
   ++c->sweeps;
   if (fit_out) {
@@ -230,8 +251,30 @@ void tucker_free(tucker_ctx *c) {
   if (!c) return;
   cudaDeviceSynchronize();
   for (void *p : c->c.allocs) cudaFree(p);
+  for (cudaEvent_t e : c->c.ev)
+    if (e) cudaEventDestroy(e);
   delete c;
 }
+
+tucker_status tucker_set_profiling(tucker_ctx *h, int enable) {
+  if (!h) return TUCKER_EINVAL;
+  h->c.profiling = enable != 0;
+  h->c.n_ev = 0;
+  return TUCKER_OK;
+}
+
+int tucker_phase_times(tucker_ctx *h, float *ms, int cap) {
+  if (!h || !ms) return -1;
+  Ctx *c = &h->c;
+  const int want = 2 * c->N + 1;
+  if (!c->profiling || c->n_ev != want + 1 || cap < want) return -1;
+  if (cudaEventSynchronize(c->ev[want]) != cudaSuccess) return -1;
+  for (int i = 0; i < want; ++i)
+    if (cudaEventElapsedTime(&ms[i], c->ev[i], c->ev[i + 1]) != cudaSuccess) return -1;
+  return want;
+}
+
+uint64_t tucker_kernel_launches(void) { return tk::g_launches.load(); }
 
 tucker_status tucker_init(tucker_ctx **out, int order, const int64_t *dims, int64_t nnz, const uint32_t *coords,
                           const float *vals, const int *ranks, const double *U0, uint64_t seed, uint32_t flags,

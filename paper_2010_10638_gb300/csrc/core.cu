@@ -94,6 +94,7 @@ void launch_core(Ctx *c, const float *Y, const double *U, double *G, cudaStream_
   const dim3 grid((unsigned)((P + 15) / 16), (unsigned)((R + 15) / 16), (unsigned)z);
   core_kernel<<<grid, 256, 0, s>>>(Y, U, I, P, R, rows_per_chunk, c->core_part, c->core_counter, G, c->norm_dev,
                                    c->norm_dev + 1, c->fit_dev);
+  ::tk::count_launch();
 }
 
 }  // namespace tk

@@ -93,9 +93,16 @@ struct Ctx {
   QrpWork qw;
   uint32_t *d_err = nullptr;   // latched device error bits
 
+  bool profiling = false;      // record CUDA events around the phases of hooi_iter
+  cudaEvent_t ev[2 * kMaxOrder + 2] = {};
+  int n_ev = 0;
+
   std::vector<void *> allocs;  // every device allocation, freed by tucker_free
   std::string last_error;
 };
+
+// ---- instrumentation: kernels launched by this library (process-wide)
+void count_launch();
 
 // ---- allocation (host-side failure injection for tests: TUCKER_FAIL_ALLOC_AT=k fails the k-th)
 cudaError_t dev_alloc(Ctx *c, void **p, size_t bytes);

@@ -446,15 +446,21 @@ static tucker_status qrp_run(const AT *A, int64_t m, int64_t n, int64_t lda, int
   if (cudaMemsetAsync(w->counter, 0, sizeof(unsigned) * 4, s) != cudaSuccess) return TUCKER_ECUDA;
   if (cudaMemsetAsync(w->F, 0, sizeof(double) * (size_t)(n * k), s) != cudaSuccess) return TUCKER_ECUDA;
   qrp_init_kernel<AT><<<g2, kQThreads, 0, s>>>(a);
+  ::tk::count_launch();
   for (int j = 0; j < k; ++j) {
     qrp_col_kernel<AT><<<nbA, kQThreads, 0, s>>>(a, j);
+    ::tk::count_launch();
     qrp_gemv_kernel<AT><<<g2, kQThreads, 0, s>>>(a, j);
+    ::tk::count_launch();
     qrp_renorm_kernel<AT><<<nbA, kQThreads, 0, s>>>(a, j);
+    ::tk::count_launch();
   }
   qrp_m_kernel<<<1, 256, 0, s>>>(a);
+  ::tk::count_launch();
   const int64_t qelems = m * k;
   const unsigned qb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((qelems + 255) / 256, (int64_t)nb * 8));
   qrp_q_kernel<<<qb, 256, sizeof(double) * (size_t)k * k, s>>>(a, Q, ldq);
+  ::tk::count_launch();
   return cudaGetLastError() == cudaSuccess ? TUCKER_OK : TUCKER_ECUDA;
 }
 
@@ -499,6 +505,7 @@ __global__ void gram_kernel(const float *Y, int64_t m, int64_t n, double *S) {
 void gram_f32(const float *Y, int64_t m, int64_t n, double *S, cudaStream_t s) {
   const dim3 g((unsigned)((m + 31) / 32), (unsigned)((m + 31) / 32));
   gram_kernel<<<g, 256, 0, s>>>(Y, m, n, S);
+  ::tk::count_launch();
 }
 
 }  // namespace tk

@@ -112,11 +112,14 @@ static void scan_rec(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *tmp
   int64_t nb = cdiv(n, kScanTile);
   if (nb == 1) {
     scan_block_kernel<<<1, kScanThreads, 0, s>>>(in, out, n, total);
+    ::tk::count_launch();
     return;
   }
   scan_block_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, tmp);
+  ::tk::count_launch();
   scan_rec(tmp, tmp, nb, tmp + nb + 1, total, s);
   scan_add_kernel<<<(unsigned)nb, 256, 0, s>>>(out, n, tmp);
+  ::tk::count_launch();
 }
 
 void exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *tmp, cudaStream_t s) {
@@ -227,8 +230,10 @@ static void radix_sort_perm(const uint32_t *key, int bits, int64_t n, uint32_t *
   for (int shift = 0; shift < bits; shift += 8) {
     uint32_t *out = (*perm == pa) ? pb : pa;
     radix_hist_kernel<<<(unsigned)nb, kRsThreads, 0, s>>>(key, *perm, n, shift, hist);
+    ::tk::count_launch();
     exclusive_scan_u32(hist, hist, 256 * nb, tmp, s);
     radix_scatter_kernel<<<(unsigned)nb, kRsThreads, 0, s>>>(key, *perm, out, n, shift, hist);
+    ::tk::count_launch();
     *perm = out;
   }
 }
@@ -446,6 +451,7 @@ tucker_status build_sorted_copies(Ctx *c, const uint32_t *coords_in, const float
   if (n_in > 0) {
     validate_kernel<<<std::min<unsigned>(grid_for(n_in), (unsigned)c->num_sms * 8), 256, 0, s>>>(
         N, n_in, coords_in, vals_in, d_dims, c->d_err);
+    ::tk::count_launch();
     TK_TRY(cudaGetLastError());
     uint32_t err = 0;
     tucker_status st = read_u32(c, c->d_err, &err, s);
@@ -481,6 +487,7 @@ tucker_status build_sorted_copies(Ctx *c, const uint32_t *coords_in, const float
   uint32_t nout = 0;
   if (n_in > 0) {
     mark_new_kernel<<<grid_for(n_in), 256, 0, s>>>(N, n_in, coords_in, perm, flag);
+    ::tk::count_launch();
     exclusive_scan_total(flag, pos, n_in, stmp, d_small, s);
     tucker_status st = read_u32(c, d_small, &nout, s);
     if (st != TUCKER_OK) return st;
@@ -496,8 +503,11 @@ tucker_status build_sorted_copies(Ctx *c, const uint32_t *coords_in, const float
   if (n_in > 0) {
     coalesce_kernel<<<grid_for(n_in), 256, 0, s>>>(N, n_in, coords_in, vals_in, perm, flag, pos, Z, c->coords, c->vals,
                                                     sq);
+    ::tk::count_launch();
     reduce_f64_partial<<<kRedBlocks, 256, 0, s>>>(sq, Z, part);
+    ::tk::count_launch();
     reduce_f64_final<<<1, 256, 0, s>>>(part, kRedBlocks, c->norm_dev);
+    ::tk::count_launch();
     TK_TRY(cudaGetLastError());
     TK_TRY(cudaMemcpyAsync(&c->norm2, c->norm_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
     TK_TRY(cudaStreamSynchronize(s));
@@ -537,7 +547,9 @@ tucker_status build_sorted_copies(Ctx *c, const uint32_t *coords_in, const float
     uint32_t S = 0;
     if (Z > 0) {
       gather_mode_kernel<<<grid_for(Z), 256, 0, s>>>(Z, mperm, g, c->coords + (int64_t)n * Z, row, c->vals, mc.val);
+      ::tk::count_launch();
       slice_start_kernel<<<grid_for(Z), 256, 0, s>>>(Z, row, flag);
+      ::tk::count_launch();
       exclusive_scan_total(flag, pos, Z, stmp, d_small, s);
       tucker_status st = read_u32(c, d_small, &S, s);
       if (st != TUCKER_OK) return st;
@@ -550,22 +562,28 @@ tucker_status build_sorted_copies(Ctx *c, const uint32_t *coords_in, const float
     TK_TRY(cudaMemsetAsync(present, 0, sizeof(uint32_t) * (size_t)mc.I, s));
     if (Z > 0) {
       slice_write_kernel<<<grid_for(Z), 256, 0, s>>>(Z, row, flag, pos, mc.sptr, mc.sid, present, S);
+      ::tk::count_launch();
     } else {
       TK_TRY(cudaMemsetAsync(mc.sptr, 0, sizeof(uint32_t), s));
     }
     // empty rows
     invert_flag_kernel<<<grid_for(mc.I), 256, 0, s>>>(mc.I, present, flag);
+    ::tk::count_launch();
     exclusive_scan_total(flag, pos, mc.I, stmp, d_small + 1, s);
     uint32_t ne = 0;
     tucker_status st = read_u32(c, d_small + 1, &ne, s);
     if (st != TUCKER_OK) return st;
     mc.n_empty = ne;
     TK_TRY(dev_alloc(c, &mc.empty, (size_t)std::max<uint32_t>(ne, 1)));
-    if (ne) compact_kernel<<<grid_for(mc.I), 256, 0, s>>>(mc.I, flag, pos, mc.empty);
+    if (ne) {
+      compact_kernel<<<grid_for(mc.I), 256, 0, s>>>(mc.I, flag, pos, mc.empty);
+      ::tk::count_launch();
+    }
     // work units
     uint32_t nunits = 0, nlong = 0;
     if (S > 0) {
       unit_count_kernel<<<grid_for(S), 256, 0, s>>>(S, mc.sptr, (uint32_t)mc.chunk, nu, islong);
+      ::tk::count_launch();
       exclusive_scan_total(nu, uoff, S, stmp, d_small + 2, s);
       exclusive_scan_total(islong, lid, S, stmp, d_small + 3, s);
       uint32_t h2[2];
@@ -582,9 +600,11 @@ tucker_status build_sorted_copies(Ctx *c, const uint32_t *coords_in, const float
     TK_TRY(dev_alloc(c, &mc.long_k, (size_t)std::max<uint32_t>(nlong, 1)));
     TK_TRY(dev_alloc(c, &mc.long_u0, (size_t)std::max<uint32_t>(nlong, 1)));
     TK_TRY(dev_alloc(c, &mc.long_np, (size_t)std::max<uint32_t>(nlong, 1)));
-    if (S > 0)
+    if (S > 0) {
       unit_write_kernel<<<grid_for(S), 256, 0, s>>>(S, mc.sptr, (uint32_t)mc.chunk, nu, uoff, islong, lid, mc.unit_e0,
                                                      mc.unit_k0, mc.unit_slot, mc.long_k, mc.long_u0, mc.long_np);
+      ::tk::count_launch();
+    }
     TK_TRY(cudaGetLastError());
   }
   TK_TRY(cudaStreamSynchronize(s));

@@ -365,6 +365,7 @@ static cudaError_t run_fast(const TtmcParams &p, cudaStream_t s) {
   }
   const unsigned blocks = (unsigned)((p.n_units + kTtmcWarps - 1) / kTtmcWarps);
   kern<<<blocks, kTtmcWarps * 32, smem, s>>>(p);
+  ::tk::count_launch();
   return cudaGetLastError();
 }
 
@@ -374,6 +375,7 @@ static cudaError_t run_generic(const TtmcParams &p, cudaStream_t s) {
   const unsigned blocks = (unsigned)((p.n_units + kTtmcWarps - 1) / kTtmcWarps);
   const unsigned cols = (unsigned)((p.P + 32 * CPL - 1) / (32 * CPL));
   ttmc_generic_kernel<CPL, FT><<<dim3(blocks, cols), kTtmcWarps * 32, 0, s>>>(p);
+  ::tk::count_launch();
   return cudaGetLastError();
 }
 
@@ -442,11 +444,13 @@ tucker_status launch_ttmc(Ctx *c, int mode, float *Y, cudaStream_t s) {
   if (mc.n_long > 0) {
     ttmc_fixup_kernel<<<(unsigned)mc.n_long, 256, 0, s>>>(mc.long_k, mc.long_u0, mc.long_np, mc.sid, c->carry, Y,
                                                           mc.P);
+    ::tk::count_launch();
     TK_CUDA(cudaGetLastError());
   }
   if (mc.n_empty > 0) {
     ttmc_zero_rows_kernel<<<(unsigned)std::min<int64_t>(mc.n_empty, 65535), 256, 0, s>>>(mc.empty, mc.n_empty, Y,
                                                                                         mc.P);
+    ::tk::count_launch();
     TK_CUDA(cudaGetLastError());
   }
   return TUCKER_OK;

@@ -33,7 +33,8 @@ STATUS = {0: "TUCKER_OK", 1: "TUCKER_EINVAL", 2: "TUCKER_ERANK", 3: "TUCKER_ENOM
 
 EXPORTS = ["tucker_init", "ttmc_mode", "qrp_leading", "qrp_leading_work_bytes", "hooi_iter", "core_tensor",
            "tucker_get_factor", "tucker_set_factor", "tucker_loss_grad", "tucker_nnz", "tucker_norm2",
-           "tucker_sync_status", "tucker_free", "tucker_status_str", "tucker_last_error"]
+           "tucker_sync_status", "tucker_free", "tucker_status_str", "tucker_last_error", "tucker_set_profiling",
+           "tucker_phase_times", "tucker_kernel_launches"]
 
 
 class TuckerError(RuntimeError):
@@ -78,6 +79,12 @@ def load(path: str = LIB_PATH):
     lib.tucker_status_str.restype = ctypes.c_char_p
     lib.tucker_last_error.argtypes = [vp]
     lib.tucker_last_error.restype = ctypes.c_char_p
+    lib.tucker_set_profiling.argtypes = [vp, cint]
+    lib.tucker_set_profiling.restype = cint
+    lib.tucker_phase_times.argtypes = [vp, P(ctypes.c_float), cint]
+    lib.tucker_phase_times.restype = cint
+    lib.tucker_kernel_launches.argtypes = []
+    lib.tucker_kernel_launches.restype = ctypes.c_uint64
     for name in ("tucker_init", "ttmc_mode", "qrp_leading", "hooi_iter", "core_tensor", "tucker_get_factor",
                  "tucker_set_factor", "tucker_loss_grad", "tucker_sync_status"):
         getattr(lib, name).restype = cint
@@ -285,3 +292,21 @@ def qrp_leading(A: torch.Tensor, k: int, work: torch.Tensor | None = None, strea
     _check(lib.qrp_leading(A.data_ptr(), m, n, n, int(k), Q.data_ptr(), piv.data_ptr(), rdiag.data_ptr(),
                            work.data_ptr(), work.numel(), _stream(stream)), "qrp_leading")
     return Q, piv, rdiag
+
+
+def tucker_set_profiling(ctx: Context, enable: bool = True) -> None:
+    _check(load().tucker_set_profiling(ctx.handle, int(bool(enable))), "tucker_set_profiling", ctx)
+
+
+def tucker_phase_times(ctx: Context):
+    """Per-phase milliseconds of the latest profiled sweep: [ttmc_1, qrp_1, ..., ttmc_N, qrp_N, core]."""
+    n = 2 * ctx.N + 1
+    buf = (ctypes.c_float * n)()
+    got = load().tucker_phase_times(ctx.handle, buf, n)
+    if got != n:
+        raise TuckerError(6, "tucker_phase_times", "profiling off or no complete sweep")
+    return [float(x) for x in buf]
+
+
+def tucker_kernel_launches() -> int:
+    return int(load().tucker_kernel_launches())
