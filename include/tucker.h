@@ -117,6 +117,26 @@ TUCKER_API tucker_status qrp_leading(const double *A, int64_t m, int64_t n, int6
 TUCKER_API size_t qrp_leading_work_bytes(int64_t m, int64_t n, int k);
 
 /*
+ * qrp_leading_noalloc — qrp_leading without caller-provided scratch, for callers that
+ * cannot allocate device memory at all: a host program that hands all of its device
+ * memory to another allocator when it starts, or a latency-bound loop that must never
+ * call cudaMalloc/cudaFree (both can synchronise the whole device).  The paper has no
+ * counterpart; the arithmetic, arguments and results are those of qrp_leading.
+ *
+ * The scratch is a fixed device array of qrp_leading_noalloc_max_bytes() bytes
+ * (16 MiB) that every GPU loading this library holds until the process exits.  Sizes
+ * with qrp_leading_work_bytes(m, n, k) above that limit return TUCKER_EINVAL.  No
+ * device memory is allocated by the call.  The first call on a device looks up the
+ * array's device address (once per device, with that device current); make that
+ * first call before any stream capture.  All calls share the array: whatever must
+ * start at zero is cleared by each call, and calls that overlap on the GPU (different
+ * streams, or different host threads on one device) race on it.
+ */
+TUCKER_API tucker_status qrp_leading_noalloc(const double *A, int64_t m, int64_t n, int64_t lda, int k,
+                                             double *Q, int64_t *piv, double *rdiag, void *stream);
+TUCKER_API size_t qrp_leading_noalloc_max_bytes(void);
+
+/*
  * hooi_iter — one sweep of Algorithm 2: for n = 1..N, Y_(n) by ttmc_mode and
  * U_n <- the first R_n columns of Q from QRP of Y_(n) (of Y_(n) Y_(n)^T when
  * P_n > I_n, unless TUCKER_F_QRP_DIRECT); then the core G = Y_(N) x_N U_N^T and

@@ -34,7 +34,7 @@ STATUS = {0: "TUCKER_OK", 1: "TUCKER_EINVAL", 2: "TUCKER_ERANK", 3: "TUCKER_ENOM
 EXPORTS = ["tucker_init", "ttmc_mode", "qrp_leading", "qrp_leading_work_bytes", "hooi_iter", "core_tensor",
            "tucker_get_factor", "tucker_set_factor", "tucker_loss_grad", "tucker_nnz", "tucker_norm2",
            "tucker_sync_status", "tucker_free", "tucker_status_str", "tucker_last_error", "tucker_set_profiling",
-           "tucker_phase_times", "tucker_kernel_launches"]
+           "tucker_phase_times", "tucker_kernel_launches", "qrp_leading_noalloc", "qrp_leading_noalloc_max_bytes"]
 
 
 class TuckerError(RuntimeError):
@@ -83,6 +83,10 @@ def load(path: str = LIB_PATH):
     lib.tucker_set_profiling.restype = cint
     lib.tucker_phase_times.argtypes = [vp, P(ctypes.c_float), cint]
     lib.tucker_phase_times.restype = cint
+    lib.qrp_leading_noalloc.argtypes = [vp, i64, i64, i64, cint, vp, vp, vp, vp]
+    lib.qrp_leading_noalloc.restype = cint
+    lib.qrp_leading_noalloc_max_bytes.argtypes = []
+    lib.qrp_leading_noalloc_max_bytes.restype = csz
     lib.tucker_kernel_launches.argtypes = []
     lib.tucker_kernel_launches.restype = ctypes.c_uint64
     for name in ("tucker_init", "ttmc_mode", "qrp_leading", "hooi_iter", "core_tensor", "tucker_get_factor",
@@ -310,3 +314,20 @@ def tucker_phase_times(ctx: Context):
 
 def tucker_kernel_launches() -> int:
     return int(load().tucker_kernel_launches())
+
+
+def qrp_leading_noalloc_max_bytes() -> int:
+    return int(load().qrp_leading_noalloc_max_bytes())
+
+
+def qrp_leading_noalloc(A: torch.Tensor, k: int, stream=None):
+    """qrp_leading with the library's fixed device scratch (no scratch argument, no
+    device allocation inside the call).  Returns (Q, piv, rdiag) like qrp_leading."""
+    _dev(A, torch.float64, "A")
+    m, n = A.shape
+    Q = torch.empty((m, k), dtype=torch.float64, device="cuda")
+    piv = torch.empty(k, dtype=torch.int64, device="cuda")
+    rdiag = torch.empty(k, dtype=torch.float64, device="cuda")
+    _check(load().qrp_leading_noalloc(A.data_ptr(), m, n, n, int(k), Q.data_ptr(), piv.data_ptr(), rdiag.data_ptr(),
+                                      _stream(stream)), "qrp_leading_noalloc")
+    return Q, piv, rdiag
