@@ -196,6 +196,7 @@ static tucker_status hooi_impl(Ctx *c, double *fit_out, cudaStream_t s) {
     const int ncols = qrp_n_cols(c, n);
     QrpWork w;
     qrp_bind_work(&w, c->qw.V, mc.I, ncols, k, c->num_sms);
+    w.err_out = c->d_err;  // a timed-out wait is reported by the next synchronising call
     if (ncols == mc.I && mc.P > mc.I) {
       gram_f32(c->Y, mc.I, mc.P, c->gram, s);
       st = qrp_run_f64(c->gram, mc.I, mc.I, mc.I, k, c->U64[n], k, nullptr, nullptr, &w, c->num_sms, s);

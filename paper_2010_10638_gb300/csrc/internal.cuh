@@ -57,6 +57,9 @@ struct QrpWork {
   double *scal = nullptr;    // scalars: [0] tau, [1] beta, [2] v_jj, [3..] misc
   int *iscal = nullptr;      // int scalars: [0] pivot, [1] number of flagged columns, [2..3] counters
   unsigned *counter = nullptr;  // last-block counters
+  int *nflag = nullptr;      // [64] per-step count of columns whose norm is recomputed
+  unsigned *bar = nullptr;   // [4] grid barrier: arrivals, generation, error word, spare
+  uint32_t *err_out = nullptr;  // where a timed-out barrier is reported (default &bar[2])
   size_t bytes = 0;
 };
 

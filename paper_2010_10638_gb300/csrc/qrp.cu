@@ -358,6 +358,584 @@ __global__ void qrp_q_kernel(QrpArgs a, double *Q, int64_t ldq) {
   }
 }
 
+// ============================================================================ persistent form
+// One cooperative launch runs all k steps.  Blocks own a contiguous range of rows for
+// the row-parallel phases and a strided set of column positions for the column
+// phases; three grid barriers separate the phases of a step:
+//   A  rows of the updated pivot column -> V[:, j], partial ||.||^2   | barrier
+//      every block forms tau, beta, v_jj from the same partials (identical values)
+//   B  partial A^T v_j (all columns) and V^T v_j                      | barrier
+//   C  per column: F[c, j], R[j, c], norm downdate (warp per column)   | barrier
+//      [rare: exact recomputation of cancelled norms, two more barriers]
+//      every block picks the next pivot from the same norms and swaps it in its own
+//      shared-memory copy of the column order, so the swap needs no barrier.
+// F, vn, vref and flag are indexed by original column, so nothing global is swapped.
+// For FP32 input, A^T v accumulates exact FP32 products (a * v_hi split by FMA) in a
+// double-float pair (TwoSum), flushed to FP64 every 256 rows; FP64 input uses DFMA.
+// Data written by other blocks during the launch is read with ld.global.cg (L2).
+// Every barrier wait is bounded; on a timeout the kernel records kErrTimeout, fills
+// rdiag with NaN and returns.
+constexpr int kPThreads = 256;
+constexpr int kPWarps = kPThreads / 32;
+constexpr int kPStage = 2048;  // rows of v staged in shared memory at a time
+constexpr unsigned long long kSpinLimit = 1ull << 25;
+
+struct PArgs {
+  const void *A;
+  int64_t m, n, lda;
+  int k;
+  double *V, *F, *part, *vn, *vref, *T, *Q;
+  int64_t ldq;
+  int *flag, *nflag;
+  unsigned *bar;   // [0] arrivals, [1] generation, [2] abort flag (cleared per call)
+  uint32_t *err;   // where a timeout is reported (the context's error word, or bar[2])
+  int64_t *piv;
+  double *rdiag;
+  int64_t part_ld;
+};
+
+__device__ __forceinline__ bool grid_sync(const PArgs &a) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *gen = a.bar + 1;
+    const unsigned g0 = *gen;
+    __threadfence();
+    const unsigned t = atomicAdd(a.bar, 1u);
+    if (t == gridDim.x - 1u) {
+      atomicExch(a.bar, 0u);
+      __threadfence();
+      atomicAdd(a.bar + 1, 1u);
+    } else {
+      unsigned long long spins = 0;
+      while (*gen == g0) {
+        if (++spins > kSpinLimit) {
+          atomicOr(a.bar + 2, 1u);
+          atomicOr(a.err, kErrTimeout);
+          break;
+        }
+        if ((spins & 1023u) == 0u && *(volatile unsigned *)(a.bar + 2)) break;  // another block gave up
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    ok = *(volatile unsigned *)(a.bar + 2) == 0u;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+__device__ __forceinline__ void timeout_exit(const PArgs &a) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+    if (a.rdiag)
+      for (int j = 0; j < a.k; ++j) a.rdiag[j] = qnan;
+    a.Q[0] = qnan;  // a factor with a NaN makes the failure visible downstream
+  }
+}
+
+// double-float accumulation of exact FP32 products: s += a * (bh + bl)
+struct DF {
+  float hi = 0.f, lo = 0.f;
+};
+__device__ __forceinline__ void df_fma(DF &s, float a, float bh, float bl) {
+  const float p = a * bh;
+  const float e = fmaf(a, bh, -p);
+  const float q = a * bl;
+  const float t = s.hi + p;
+  const float bp = t - s.hi;
+  const float err = (s.hi - (t - bp)) + (p - bp);
+  s.hi = t;
+  s.lo += err + (e + q);
+}
+
+__device__ __forceinline__ double block_sum_p(double v, double *red) {
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = kPThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// Row-split, column-parallel reduction of sum_i f(A[i, c]) * v_i over this block's rows
+// [r0, r1) for every column c; results to part[b * ld + c].  v_i (FP64) comes from
+// vfun(i); with FP32 A it is split into hi/lo floats and accumulated in double-float.
+template <typename AT, bool SQUARE, typename VF>
+__device__ void colsum_rows(const PArgs &a, int64_t r0, int64_t r1, VF vfun, double *red, void *stage) {
+  const int64_t n = a.n;
+  int cw = 32;
+  while (cw < n && cw < kPThreads) cw <<= 1;
+  const int nrl = kPThreads / cw, cl = threadIdx.x % cw, rl = threadIdx.x / cw;
+  for (int64_t c0 = 0; c0 < n; c0 += cw) {
+    const int64_t c = c0 + cl;
+    double acc = 0.0;
+    for (int64_t s0 = r0; s0 < r1; s0 += kPStage) {
+      const int64_t s1 = min(r1, s0 + kPStage);
+      if (!SQUARE) {  // stage v for rows [s0, s1)
+        __syncthreads();
+        for (int64_t i = s0 + threadIdx.x; i < s1; i += kPThreads) {
+          const double v = vfun(i);
+          if constexpr (sizeof(AT) == 4) {
+            const float h = (float)v;
+            reinterpret_cast<float2 *>(stage)[i - s0] = make_float2(h, (float)(v - (double)h));
+          } else {
+            reinterpret_cast<double *>(stage)[i - s0] = v;
+          }
+        }
+        __syncthreads();
+      }
+      if (c < n) {
+        if constexpr (sizeof(AT) == 4) {
+          const float *A = static_cast<const float *>(a.A);
+          for (int64_t q0 = s0 + rl; q0 < s1; q0 += (int64_t)nrl * 256) {
+            DF d;
+            const int64_t q1 = min(s1, q0 + (int64_t)nrl * 256);
+            for (int64_t i = q0; i < q1; i += nrl) {
+              const float x = __ldg(A + i * a.lda + c);
+              if (SQUARE) {
+                df_fma(d, x, x, 0.f);
+              } else {
+                const float2 vv = reinterpret_cast<const float2 *>(stage)[i - s0];
+                df_fma(d, x, vv.x, vv.y);
+              }
+            }
+            acc += (double)d.hi + (double)d.lo;
+          }
+        } else {
+          const double *A = static_cast<const double *>(a.A);
+          for (int64_t i = s0 + rl; i < s1; i += nrl) {
+            const double x = __ldg(A + i * a.lda + c);
+            acc = fma(x, SQUARE ? x : reinterpret_cast<const double *>(stage)[i - s0], acc);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    if (rl == 0 && c < n) {
+      double t = 0.0;
+      for (int q = 0; q < nrl; ++q) t += red[q * cw + cl];
+      a.part[(int64_t)blockIdx.x * a.part_ld + c] = t;
+    }
+  }
+  __syncthreads();
+}
+
+// FP32 A with n % 4 == 0 and lda % 4 == 0: each thread owns four adjacent columns (one
+// float4 per row) and issues 8 rows of loads before using them, so that enough bytes
+// are in flight per SM to stream A at memory speed; four independent double-float
+// accumulators per thread.  Same results layout as colsum_rows.
+template <bool SQUARE, typename VF>
+__device__ void colsum_rows_f32x4(const PArgs &a, int64_t r0, int64_t r1, VF vfun, double *red4, float2 *stage) {
+  const int64_t nq = a.n / 4, ld4 = a.lda / 4;
+  int cw = 8;
+  while (cw < nq && cw < kPThreads) cw <<= 1;
+  const int nrl = kPThreads / cw, cq = threadIdx.x % cw, rl = threadIdx.x / cw;
+  const float4 *A4 = static_cast<const float4 *>(a.A);
+  for (int64_t q0 = 0; q0 < nq; q0 += cw) {
+    const int64_t qc = q0 + cq;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t s0 = r0; s0 < r1; s0 += kPStage) {
+      const int64_t s1 = min(r1, s0 + kPStage);
+      if (!SQUARE) {
+        __syncthreads();
+        for (int64_t i = s0 + threadIdx.x; i < s1; i += kPThreads) {
+          const double v = vfun(i);
+          const float h = (float)v;
+          stage[i - s0] = make_float2(h, (float)(v - (double)h));
+        }
+        __syncthreads();
+      }
+      if (qc < nq) {
+        const float4 *col = A4 + s0 * ld4 + qc;
+        const int cnt = (int)(s1 - s0);
+        for (int c0 = rl; c0 < cnt; c0 += nrl * 256) {  // flush the double-float pairs every 256 rows
+          DF d0, d1, d2, d3;
+          const int c1 = min(cnt, c0 + nrl * 256);
+          int ii = c0;
+          for (; ii + 7 * nrl < c1; ii += 8 * nrl) {
+            float4 x[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) x[u] = __ldg(col + (int64_t)(ii + u * nrl) * ld4);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              if (SQUARE) {
+                df_fma(d0, x[u].x, x[u].x, 0.f);
+                df_fma(d1, x[u].y, x[u].y, 0.f);
+                df_fma(d2, x[u].z, x[u].z, 0.f);
+                df_fma(d3, x[u].w, x[u].w, 0.f);
+              } else {
+                const float2 vv = stage[ii + u * nrl];
+                df_fma(d0, x[u].x, vv.x, vv.y);
+                df_fma(d1, x[u].y, vv.x, vv.y);
+                df_fma(d2, x[u].z, vv.x, vv.y);
+                df_fma(d3, x[u].w, vv.x, vv.y);
+              }
+            }
+          }
+          for (; ii < c1; ii += nrl) {
+            const float4 x = __ldg(col + (int64_t)ii * ld4);
+            const float2 vv = SQUARE ? make_float2(0.f, 0.f) : stage[ii];
+            df_fma(d0, x.x, SQUARE ? x.x : vv.x, vv.y);
+            df_fma(d1, x.y, SQUARE ? x.y : vv.x, vv.y);
+            df_fma(d2, x.z, SQUARE ? x.z : vv.x, vv.y);
+            df_fma(d3, x.w, SQUARE ? x.w : vv.x, vv.y);
+          }
+          acc[0] += (double)d0.hi + (double)d0.lo;
+          acc[1] += (double)d1.hi + (double)d1.lo;
+          acc[2] += (double)d2.hi + (double)d2.lo;
+          acc[3] += (double)d3.hi + (double)d3.lo;
+        }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) red4[q * kPThreads + threadIdx.x] = acc[q];
+    __syncthreads();
+    if (rl == 0 && qc < nq) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        double t = 0.0;
+        for (int r = 0; r < nrl; ++r) t += red4[q * kPThreads + r * cw + cq];
+        a.part[(int64_t)blockIdx.x * a.part_ld + 4 * qc + q] = t;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// sum over blocks of part[b * ld + col] by one warp (fixed order: lane-strided, then tree)
+__device__ __forceinline__ double warp_part_sum(const PArgs &a, int64_t col) {
+  const int lane = threadIdx.x & 31;
+  double t = 0.0;
+#pragma unroll 4
+  for (int bb = lane; bb < (int)gridDim.x; bb += 32) t += __ldcg(a.part + (int64_t)bb * a.part_ld + col);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  return t;
+}
+
+template <typename AT>
+__device__ __forceinline__ double aval(const PArgs &a, int64_t i, int64_t c) {
+  return (double)__ldg(static_cast<const AT *>(a.A) + i * a.lda + c);
+}
+
+// argmax of vn over positions [j0, n) in this block's column order (lowest position on
+// ties); swaps it into position j0 of perm_s.  Identical in every block.
+__device__ void pick_pivot(const PArgs &a, int *perm_s, int j0, double *red, int *redi) {
+  double best = -1.0;
+  int bi = INT_MAX;
+  for (int64_t pos = j0 + threadIdx.x; pos < a.n; pos += kPThreads) {
+    const double v = __ldcg(a.vn + perm_s[pos]);
+    if (v > best) {
+      best = v;
+      bi = (int)pos;
+    }
+  }
+  red[threadIdx.x] = best;
+  redi[threadIdx.x] = bi;
+  __syncthreads();
+  for (int o = kPThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      const double v2 = red[threadIdx.x + o];
+      const int i2 = redi[threadIdx.x + o];
+      if (v2 > red[threadIdx.x] || (v2 == red[threadIdx.x] && i2 < redi[threadIdx.x])) {
+        red[threadIdx.x] = v2;
+        redi[threadIdx.x] = i2;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const int p = redi[0];
+    if (p != j0 && p < a.n) {
+      const int t = perm_s[j0];
+      perm_s[j0] = perm_s[p];
+      perm_s[p] = t;
+    }
+  }
+  __syncthreads();
+}
+
+template <typename AT>
+__global__ void __launch_bounds__(kPThreads) qrp_persistent_kernel(PArgs a) {
+  extern __shared__ __align__(16) unsigned char psm[];
+  __shared__ double red[kPThreads];
+  __shared__ int redi[kPThreads];
+  __shared__ double s_u[64];
+  __shared__ double s_f[64];
+  __shared__ double s_v0, s_tau;
+  __shared__ int s_nflag;
+  const int64_t n = a.n, m = a.m;
+  const int k = a.k;
+  int *perm_s = reinterpret_cast<int *>(psm);
+  void *stage = psm + ((n * sizeof(int) + 15) & ~(size_t)15);
+  const int nb = gridDim.x, b = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t rows_per = (m + nb - 1) / nb;
+  const int64_t r0 = min(m, (int64_t)b * rows_per), r1 = min(m, r0 + rows_per);
+  const int64_t ld = a.part_ld;
+  const int64_t gw = (int64_t)b * kPWarps + warp, nw = (int64_t)nb * kPWarps;
+
+  __shared__ double red4[4 * kPThreads];
+  const bool vec4 = sizeof(AT) == 4 && (n % 4) == 0 && (a.lda % 4) == 0 &&
+                    (reinterpret_cast<uintptr_t>(a.A) % 16) == 0;
+  // ---- initial column norms
+  if (vec4)
+    colsum_rows_f32x4<true>(a, r0, r1, [](int64_t) { return 0.0; }, red4, static_cast<float2 *>(stage));
+  else
+    colsum_rows<AT, true>(a, r0, r1, [](int64_t) { return 0.0; }, red, stage);
+  for (int64_t c = threadIdx.x; c < n; c += kPThreads) perm_s[c] = (int)c;
+  if (!grid_sync(a)) return timeout_exit(a);
+  for (int64_t c = gw; c < n; c += nw) {
+    const double t = warp_part_sum(a, c);
+    if (lane == 0) {
+      a.vn[c] = t;
+      a.vref[c] = t;
+      a.flag[c] = 0;
+    }
+  }
+  if (b == 0)
+    for (int q = threadIdx.x; q < k * k; q += kPThreads) a.T[q] = 0.0;
+  if (!grid_sync(a)) return timeout_exit(a);
+  pick_pivot(a, perm_s, 0, red, redi);
+
+  const double tol = sqrt(DBL_EPSILON);
+  for (int j = 0; j < k; ++j) {
+    const int c0 = perm_s[j];
+    // ---- A: pivot column rows
+    if (threadIdx.x < j) s_f[threadIdx.x] = __ldcg(a.F + (int64_t)c0 * k + threadIdx.x);
+    __syncthreads();
+    double s2 = 0.0;
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += kPThreads) {
+      double y = aval<AT>(a, i, c0);
+      const double *vrow = a.V + i * k;
+      if ((k & 1) == 0) {  // rows are 16-byte aligned: independent double2 loads
+        const double2 *v2 = reinterpret_cast<const double2 *>(vrow);
+        double2 buf[8];
+        for (int l0 = 0; l0 < j; l0 += 16) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            if (l0 + 2 * q < j) buf[q] = __ldcg(v2 + (l0 >> 1) + q);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            if (l0 + 2 * q < j) y = fma(-buf[q].x, s_f[l0 + 2 * q], y);
+            if (l0 + 2 * q + 1 < j) y = fma(-buf[q].y, s_f[l0 + 2 * q + 1], y);
+          }
+        }
+      } else {
+#pragma unroll 8
+        for (int l = 0; l < j; ++l) y = fma(-__ldcg(vrow + l), s_f[l], y);
+      }
+      y = (i >= j) ? y : 0.0;
+      s2 = fma(y, y, s2);
+      a.V[i * k + j] = y;
+    }
+    s2 = block_sum_p(s2, red);
+    if (threadIdx.x == 0) a.part[(int64_t)b * ld + n + k] = s2;
+    if (!grid_sync(a)) return timeout_exit(a);
+    // ---- reflector scalars, identically in every block
+    {
+      double t = 0.0;
+      for (int bb = threadIdx.x; bb < nb; bb += kPThreads) t += __ldcg(a.part + (int64_t)bb * ld + n + k);
+      const double a2 = block_sum_p(t, red);
+      if (threadIdx.x == 0) {
+        const double alpha = sqrt(a2);
+        const double x0 = __ldcg(a.V + (int64_t)j * k + j);
+        double tau = 0.0, beta = 0.0, v0 = 0.0;
+        if (alpha > 0.0) {
+          const double sg = (x0 < 0.0) ? -1.0 : 1.0;
+          v0 = x0 + sg * alpha;
+          tau = 2.0 / (2.0 * alpha * (alpha + fabs(x0)));
+          beta = -sg * alpha;
+        }
+        s_v0 = v0;
+        s_tau = tau;
+        if (b == 0) {
+          if (a.rdiag) a.rdiag[j] = beta;
+          if (a.piv) a.piv[j] = c0;
+          a.nflag[j] = 0;
+        }
+      }
+      __syncthreads();
+    }
+    const double v0 = s_v0, tau = s_tau;
+    // ---- B: A^T v_j and V^T v_j over this block's rows (v_j is zero above row j)
+    const int64_t rb0 = max(r0, (int64_t)j);
+    auto vfun = [&](int64_t i) { return (i == j) ? v0 : __ldcg(a.V + i * k + j); };
+    if (vec4)
+      colsum_rows_f32x4<false>(a, rb0, max(rb0, r1), vfun, red4, static_cast<float2 *>(stage));
+    else
+      colsum_rows<AT, false>(a, rb0, max(rb0, r1), vfun, red, stage);
+    for (int l = warp; l < j; l += kPWarps) {
+      double t = 0.0;
+      for (int64_t i = rb0 + lane; i < r1; i += 32) t = fma(__ldcg(a.V + i * k + l), vfun(i), t);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) a.part[(int64_t)b * ld + n + l] = t;
+    }
+    if (!grid_sync(a)) return timeout_exit(a);
+    // ---- C: F[:, j], row j of R, norm downdate
+    // Row j of V gets v_jj only now: every block read x0 from it between the first two
+    // barriers of this step, and until then only its owner used v_jj (from s_v0).
+    if (threadIdx.x == 0 && j >= r0 && j < r1) a.V[(int64_t)j * k + j] = v0;
+    const bool has_cols = (int64_t)j + 1 + (int64_t)b * kPWarps < n;
+    if (has_cols || b == 0) {
+      for (int l = warp; l < j; l += kPWarps) {
+        const double t = warp_part_sum(a, n + l);
+        if (lane == 0) s_u[l] = t;
+      }
+      __syncthreads();
+    }
+    if (b == 0) {
+      for (int l = threadIdx.x; l < j; l += kPThreads) {
+        double t = 0.0;
+        for (int q = l; q < j; ++q) t = fma(__ldcg(a.T + (int64_t)l * k + q), s_u[q], t);
+        a.T[(int64_t)l * k + j] = -tau * t;
+      }
+      if (threadIdx.x == 0) a.T[(int64_t)j * k + j] = tau;
+    }
+    if (has_cols) {
+      if (threadIdx.x < j) s_f[threadIdx.x] = __ldcg(a.V + (int64_t)j * k + threadIdx.x);  // row j of V
+      __syncthreads();
+    }
+    for (int64_t pos = j + 1 + gw; pos < n; pos += nw) {
+      const int c = perm_s[pos];
+      const double w = warp_part_sum(a, c);
+      const double *frow = a.F + (int64_t)c * k;
+      double corr = 0.0, rv = 0.0;
+      for (int l = lane; l < j; l += 32) {
+        const double fl = __ldcg(frow + l);
+        corr = fma(fl, s_u[l], corr);
+        rv = fma(s_f[l], fl, rv);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        corr += __shfl_xor_sync(0xffffffffu, corr, o);
+        rv += __shfl_xor_sync(0xffffffffu, rv, o);
+      }
+      if (lane == 0) {
+        const double f = tau * (w - corr);
+        a.F[(int64_t)c * k + j] = f;
+        double r = aval<AT>(a, j, c) - rv;
+        r = fma(-v0, f, r);
+        double nv = __ldcg(a.vn + c) - r * r;
+        const double ref = __ldcg(a.vref + c);
+        if (ref > 0.0 && !(nv > tol * ref)) {
+          a.flag[c] = 1;
+          atomicAdd(a.nflag + j, 1);
+          nv = 0.0;
+        } else if (!(nv > 0.0)) {
+          nv = 0.0;
+        }
+        a.vn[c] = nv;
+      }
+    }
+    if (!grid_sync(a)) return timeout_exit(a);
+    if (threadIdx.x == 0) s_nflag = *(volatile int *)(a.nflag + j);
+    __syncthreads();
+    if (s_nflag > 0) {  // exact recomputation of cancelled norms (uniform decision)
+      const int64_t rr0 = max(r0, (int64_t)j + 1);
+      for (int64_t pos = j + 1; pos < n; ++pos) {
+        const int c = perm_s[pos];
+        if (!__ldcg(a.flag + c)) continue;
+        double t = 0.0;
+        for (int64_t i = rr0 + threadIdx.x; i < r1; i += kPThreads) {
+          double y = aval<AT>(a, i, c);
+          for (int l = 0; l <= j; ++l) y = fma(-__ldcg(a.V + i * k + l), __ldcg(a.F + (int64_t)c * k + l), y);
+          t = fma(y, y, t);
+        }
+        t = block_sum_p(t, red);
+        if (threadIdx.x == 0) a.part[(int64_t)b * ld + c] = t;
+      }
+      if (!grid_sync(a)) return timeout_exit(a);
+      for (int64_t pos = j + 1 + gw; pos < n; pos += nw) {
+        const int c = perm_s[pos];
+        if (!__ldcg(a.flag + c)) continue;
+        const double t = warp_part_sum(a, c);
+        if (lane == 0) {
+          a.vn[c] = t;
+          a.vref[c] = t;
+          a.flag[c] = 0;
+        }
+      }
+      if (!grid_sync(a)) return timeout_exit(a);
+    }
+    if (j + 1 < k) pick_pivot(a, perm_s, j + 1, red, redi);
+  }
+
+  // ---- Q = [I_k; 0] - V (T V[0:k, :]^T), rows of this block
+  double *Ms = reinterpret_cast<double *>(stage);
+  for (int q = threadIdx.x; q < k * k; q += kPThreads) {
+    const int l = q / k, cc = q % k;
+    double t = 0.0;
+    for (int p = l; p <= cc; ++p) t = fma(__ldcg(a.T + (int64_t)l * k + p), __ldcg(a.V + (int64_t)cc * k + p), t);
+    Ms[q] = t;
+  }
+  __syncthreads();
+  for (int64_t idx = r0 * k + threadIdx.x; idx < r1 * k; idx += kPThreads) {
+    const int64_t i = idx / k;
+    const int cc = (int)(idx % k);
+    double t = (i == cc) ? 1.0 : 0.0;
+    const int lmax = (int)min((int64_t)k - 1, i);
+    for (int l = 0; l <= lmax; ++l) t = fma(-__ldcg(a.V + i * k + l), Ms[l * k + cc], t);
+    a.Q[i * a.ldq + cc] = t;
+  }
+}
+
+template <typename AT>
+static bool qrp_persistent(const AT *A, int64_t m, int64_t n, int64_t lda, int k, double *Q, int64_t ldq,
+                           int64_t *piv, double *rdiag, QrpWork *w, int nb_sms, cudaStream_t s, cudaError_t *err) {
+  *err = cudaSuccess;
+  if (n > 8192 || k > 64) return false;
+  int dev = 0, coop = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return false;
+  const size_t perm_bytes = ((size_t)n * sizeof(int) + 15) & ~(size_t)15;
+  const size_t stage_bytes = std::max<size_t>((size_t)kPStage * 8, (size_t)k * k * sizeof(double));
+  const size_t smem = perm_bytes + stage_bytes;
+  auto kern = qrp_persistent_kernel<AT>;
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return false;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPThreads, smem) != cudaSuccess || per_sm < 1)
+    return false;
+  int64_t nb = std::min<int64_t>((int64_t)per_sm * nb_sms, 2 * (int64_t)nb_sms);
+  nb = std::min<int64_t>(nb, std::max<int64_t>(1, (m * std::max<int64_t>(n, 1)) / 8192));
+  nb = std::max<int64_t>(1, std::min<int64_t>(nb, m));
+  PArgs a{};
+  a.A = A;
+  a.m = m;
+  a.n = n;
+  a.lda = lda;
+  a.k = k;
+  a.V = w->V;
+  a.F = w->F;
+  a.part = w->part;
+  a.vn = w->vn;
+  a.vref = w->vref;
+  a.T = w->T;
+  a.Q = Q;
+  a.ldq = ldq;
+  a.flag = w->flag;
+  a.nflag = w->nflag;
+  a.bar = w->bar;
+  a.err = w->err_out ? w->err_out : w->bar + 2;
+  a.piv = piv;
+  a.rdiag = rdiag;
+  a.part_ld = n + std::max(k, 1) + 8;
+  if ((*err = cudaMemsetAsync(w->bar, 0, 3 * sizeof(unsigned), s)) != cudaSuccess) return true;
+  void *args[] = {&a};
+  *err = cudaLaunchCooperativeKernel((const void *)kern, dim3((unsigned)nb), dim3(kPThreads), args, smem, s);
+  ::tk::count_launch();
+  return true;
+}
+
 // ---------------------------------------------------------------------------- host side
 int qrp_blocks(int num_sms, int64_t m) {
   int64_t b = std::max<int64_t>(1, std::min<int64_t>((int64_t)num_sms, (m + 31) / 32));
@@ -376,7 +954,7 @@ static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 // nb = target number of blocks (typically the SM count)
 size_t qrp_work_bytes(int64_t m, int64_t n, int k, int nb) {
   const int rc = row_chunks_for(2 * nb, n, m);
-  const int64_t part_rows = std::max<int64_t>(std::max<int64_t>(rc, nb), 1);
+  const int64_t part_rows = std::max<int64_t>(std::max<int64_t>(rc, 2 * (int64_t)nb), 1);
   const int64_t part_ld = n + std::max(k, 1) + 8;
   size_t b = 0;
   b += align256(sizeof(double) * (size_t)std::max<int64_t>(m * k, 1));       // V
@@ -386,12 +964,13 @@ size_t qrp_work_bytes(int64_t m, int64_t n, int k, int nb) {
   b += 2 * align256(sizeof(int) * (size_t)std::max<int64_t>(n, 1));          // perm, flag
   b += 2 * align256(sizeof(double) * (size_t)std::max(k * k, 1));           // T, M
   b += align256(sizeof(double) * 16) + align256(sizeof(int) * 16) + align256(sizeof(unsigned) * 4);
+  b += align256(sizeof(int) * 64) + align256(sizeof(unsigned) * 4);  // nflag, bar
   return b;
 }
 
 void qrp_bind_work(QrpWork *w, void *base, int64_t m, int64_t n, int k, int nb) {
   const int rc = row_chunks_for(2 * nb, n, m);
-  const int64_t part_rows = std::max<int64_t>(std::max<int64_t>(rc, nb), 1);
+  const int64_t part_rows = std::max<int64_t>(std::max<int64_t>(rc, 2 * (int64_t)nb), 1);
   const int64_t part_ld = n + std::max(k, 1) + 8;
   char *p = static_cast<char *>(base);
   auto take = [&](size_t bytes) {
@@ -411,6 +990,9 @@ void qrp_bind_work(QrpWork *w, void *base, int64_t m, int64_t n, int k, int nb) 
   w->scal = (double *)take(sizeof(double) * 16);
   w->iscal = (int *)take(sizeof(int) * 16);
   w->counter = (unsigned *)take(sizeof(unsigned) * 4);
+  w->nflag = (int *)take(sizeof(int) * 64);
+  w->bar = (unsigned *)take(sizeof(unsigned) * 4);
+  w->err_out = w->bar + 2;
   w->bytes = (size_t)(p - static_cast<char *>(base));
 }
 
@@ -419,6 +1001,11 @@ static tucker_status qrp_run(const AT *A, int64_t m, int64_t n, int64_t lda, int
                              int64_t *piv, double *rdiag, QrpWork *w, int nb, cudaStream_t s) {
   if (k == 0) return TUCKER_OK;
   if (k > 64) return TUCKER_ERANK;  // F rows are staged in 64-wide shared buffers
+  {
+    cudaError_t e = cudaSuccess;
+    if (qrp_persistent<AT>(A, m, n, lda, k, Q, ldq, piv, rdiag, w, nb, s, &e))
+      return e == cudaSuccess ? TUCKER_OK : TUCKER_ECUDA;
+  }
   QrpArgs a{};
   a.A = A;
   a.m = m;
