@@ -306,6 +306,40 @@ def run_mine(args):
                     "hooi_s_per_iter": sweep_b * 1e-3, "value": N * Zc / (sweep_b * 1e-3)}
             T.tucker_free(ctxb)
 
+    # ---- the differentiation form: loss + adjoint on the completion workload
+    adjoint = None
+    if not args.no_adjoint:
+        ci = synth.make("completion-10M")
+        cw = ci.workload
+        with torch.cuda.stream(stream):
+            ctxa = T.tucker_init(cw.dims, torch.as_tensor(ci.coords.astype(np.int32)).to(dev),
+                                 torch.as_tensor(ci.vals).to(dev), cw.ranks, [torch.as_tensor(u).to(dev) for u in ci.U0],
+                                 stream=stream)
+            rng = np.random.default_rng(7)
+            Ua = [torch.as_tensor((ci.model["U"][m] + 0.1 * rng.standard_normal(ci.model["U"][m].shape))
+                                  .astype(np.float32)).to(dev) for m in range(len(cw.dims))]
+            Ga = torch.as_tensor(ci.model["G"].astype(np.float32)).to(dev)
+            lossb = torch.empty(1, dtype=torch.float64, device=dev)
+            dUa = [torch.empty_like(u) for u in Ua]
+            dGa = torch.empty_like(Ga)
+            for _ in range(3):
+                T.tucker_loss_grad(ctxa, Ua, Ga, lossb, dUa, dGa, stream=stream)
+            evs = []
+            for i in range(10):
+                flush.fill_(float(i))
+                a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a_.record(stream)
+                T.tucker_loss_grad(ctxa, Ua, Ga, lossb, dUa, dGa, stream=stream)
+                b_.record(stream)
+                evs.append((a_, b_))
+            torch.cuda.synchronize()
+            ams = statistics.median(a_.elapsed_time(b_) for a_, b_ in evs)
+            Za = T.tucker_nnz(ctxa)
+            adjoint = {"workload": cw.name, "dims": list(cw.dims), "nnz": Za, "ranks": list(cw.ranks),
+                       "ms_per_loss_and_grad": ams, "nnz_per_s": Za / (ams * 1e-3), "loss": float(lossb.item()),
+                       "precision": "FP32 (loss accumulated in FP64)"}
+            T.tucker_free(ctxa)
+
     # ---- end to end through the C ABI from pinned host buffers: the whole decomposition
     # job of the workload (init + its sweeps + read back fit, core and factors)
     e2e = None
@@ -405,7 +439,7 @@ def run_mine(args):
             "ttmc_nnz_per_s_per_mode": [Zc / (t * 1e-3) for t in ttmc_ms],
             "roofline": dominant, "roofline_other": qrp_roof if dominant is ttmc_roof else ttmc_roof,
             "init_s": init_s, "fit_after_warmup_and_steps": fit,
-            "bf16_factor_form": bf16, "e2e": e2e, "cpu_baseline": cpu,
+            "bf16_factor_form": bf16, "adjoint_form": adjoint, "e2e": e2e, "cpu_baseline": cpu,
             "clocks": clocks, "gpu_launches": int(launches)}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -430,6 +464,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-bf16", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "mine":
         args.warmup = 3

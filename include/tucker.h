@@ -56,6 +56,7 @@ typedef enum {
 #define TUCKER_F_QRP_DIRECT 0x2u   /* fat Y_(n) (P_n > I_n): QRP on Y_(n) itself, not on Y Y^T */
 #define TUCKER_F_HOST_INPUT 0x4u   /* coords, vals and U0 given to tucker_init are host pointers */
 #define TUCKER_F_FIT_DEVICE 0x8u   /* hooi_iter writes the fit through a device pointer, no sync */
+#define TUCKER_F_SIMT_TTMC 0x10u   /* TTMc on the FP32 ALUs only (no tensor-core form) */
 
 /*
  * tucker_init — load a sparse tensor and prepare it for HOOI (Algorithm 2 input:
@@ -68,7 +69,9 @@ typedef enum {
  *   coords  [N][nnz] uint32, structure-of-arrays (coords[m*nnz + z] is i_m of entry
  *           z), 0-based; device memory, or host with TUCKER_F_HOST_INPUT
  *   vals    [nnz] float; device, or host with TUCKER_F_HOST_INPUT
- *   ranks   host array [N]: R_1..R_N, 1 <= R_n <= I_n, prod R_n <= 2^20
+ *   ranks   host array [N]: R_1..R_N, 1 <= R_n <= min(I_n, 64), prod R_n <= 2^20
+ *           (hooi_iter further needs R_n <= prod_{m != n} R_m unless Y_(n) is fat,
+ *           and returns TUCKER_ERANK otherwise)
  *   U0      initial factors, the N matrices [I_m x R_m] (FP64, row-major) one after
  *           another; device, or host with TUCKER_F_HOST_INPUT.  U0 for mode 1 is
  *           never read (mode 1 is updated first).  NULL draws each U_m from a seeded

@@ -185,6 +185,14 @@ static tucker_status mark(Ctx *c, int i, cudaStream_t s) {
 
 static tucker_status hooi_impl(Ctx *c, double *fit_out, cudaStream_t s) {
   const int N = c->N;
+  for (int n = 0; n < N; ++n) {  // QRP takes k = R_n <= min(rows, columns) of the matrix it factors
+    const int64_t I = c->dims[n], P = c->mode[n].P;
+    const bool fat = P > I && !(c->flags & TUCKER_F_QRP_DIRECT);
+    if (!fat && c->ranks[n] > P) {
+      c->last_error = "HOOI needs R_n <= prod_{m != n} R_m for QRP of Y_(n)";
+      return TUCKER_ERANK;
+    }
+  }
   tucker_status st = mark(c, 0, s);
   if (st != TUCKER_OK) return st;
   for (int n = 0; n < N; ++n) {
@@ -290,14 +298,6 @@ tucker_status tucker_init(tucker_ctx **out, int order, const int64_t *dims, int6
     if (ranks[m] < 1 || ranks[m] > dims[m] || ranks[m] > 64) return TUCKER_ERANK;
     PR *= ranks[m];
     if (PR > (1 << 20)) return TUCKER_ERANK;
-  }
-  for (int n = 0; n < order; ++n) {
-    int64_t P = 1;
-    for (int m = 0; m < order; ++m)
-      if (m != n) P *= ranks[m];
-    const bool fat = P > dims[n];
-    const bool direct = (flags & TUCKER_F_QRP_DIRECT) != 0;
-    if ((!fat || direct) && ranks[n] > P) return TUCKER_ERANK;  // k <= min(I_n, P_n)
   }
   tucker_ctx *h = new (std::nothrow) tucker_ctx();
   if (!h) return TUCKER_ENOMEM;

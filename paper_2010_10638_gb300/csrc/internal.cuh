@@ -41,6 +41,8 @@ struct ModeCopy {
   uint32_t *long_u0 = nullptr;         // [n_long] their first unit (= first partial slot)
   uint32_t *long_np = nullptr;         // [n_long] their number of units
   int64_t n_long = 0;
+  uint32_t *src = nullptr;             // [nnz] coalesced (lexicographic) index of sorted position e;
+                                       // nullptr for mode 1, whose order is the lexicographic one
 };
 
 // Workspace of the QR with column pivoting (one set, sized for the largest mode).
@@ -90,6 +92,14 @@ struct Ctx {
   double *norm_dev = nullptr;  // [0] ||X||^2, [1] ||G||^2
   double *core_part = nullptr; // block partials of the core GEMM
   unsigned *core_counter = nullptr;
+  // adjoint workspaces (allocated by the first tucker_loss_grad)
+  float *adj_e0 = nullptr;     // residuals in lexicographic order
+  float *adj_en = nullptr;     // residuals in the order of one mode's copy
+  float *adj_Y = nullptr;      // TTMc of the residual tensor (max I_n * P_n)
+  float *adj_Q = nullptr;      // U_1 G_(1) (I_1 x P_1)
+  float *adj_Gn = nullptr;     // one unfolding of G (prod R)
+  double *adj_part = nullptr;  // loss partials
+  float *adj_gpart = nullptr;  // split-K partials of dL/dG
   bool G_valid = false;
   int sweeps = 0;
 
@@ -124,6 +134,9 @@ tucker_status build_sorted_copies(Ctx *c, const uint32_t *coords, const float *v
 
 // ---- K-b: TTMc (ttmc.cu)
 tucker_status launch_ttmc(Ctx *c, int mode, float *Y, cudaStream_t s);
+// TTMc of mode `mode` with values `val` (in that mode's sorted order) and FP32 factors
+// Uf[m] (indexed by mode; Uf[mode] unused) instead of the context's own.
+tucker_status launch_ttmc_ex(Ctx *c, int mode, float *Y, const float *val, const float *const *Uf, cudaStream_t s);
 
 // ---- K-c: QRP (qrp.cu)
 size_t qrp_work_bytes(int64_t m, int64_t n, int k, int nb);

@@ -315,6 +315,11 @@ __global__ void gather_mode_kernel(int64_t n, const uint32_t *perm, GatherArgs g
   }
 }
 
+__global__ void iota_kernel(int64_t n, uint32_t *out) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = (uint32_t)e;
+}
+
 __global__ void slice_start_kernel(int64_t n, const uint32_t *row, uint32_t *flag) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
     flag[e] = (e == 0 || row[e] != row[e - 1]) ? 1u : 0u;
@@ -544,6 +549,15 @@ tucker_status build_sorted_copies(Ctx *c, const uint32_t *coords_in, const float
     TK_TRY(dev_alloc(c, &mc.val, (size_t)std::max<int64_t>(Z, 1)));
     uint32_t *mperm = nullptr;  // mode 1: the lexicographic order is already sorted by i_1
     if (n > 0) radix_sort_perm(c->coords + (int64_t)n * Z, bits_for(mc.I - 1), Z, &mperm, pa, pb, hist, stmp, s);
+    if (n > 0 && Z > 0) {
+      TK_TRY(dev_alloc(c, &mc.src, (size_t)Z));
+      if (mperm) {
+        TK_TRY(cudaMemcpyAsync(mc.src, mperm, sizeof(uint32_t) * (size_t)Z, cudaMemcpyDeviceToDevice, s));
+      } else {  // already in order (e.g. a single distinct index): identity
+        iota_kernel<<<grid_for(Z), 256, 0, s>>>(Z, mc.src);
+        ::tk::count_launch();
+      }
+    }
     uint32_t S = 0;
     if (Z > 0) {
       gather_mode_kernel<<<grid_for(Z), 256, 0, s>>>(Z, mperm, g, c->coords + (int64_t)n * Z, row, c->vals, mc.val);

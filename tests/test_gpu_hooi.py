@@ -87,3 +87,17 @@ def test_seeded_initial_factors_are_orthonormal():
         np.testing.assert_allclose(U.T @ U, np.eye(U.shape[1]), atol=1e-13)
     f = T.hooi_iter(ctx)
     assert 0.0 < f < 1.0
+
+
+def test_hooi_rejects_ranks_qrp_cannot_produce():
+    # order 2, ranks (6, 8): mode 2 would need 8 QRP columns from a 80 x 6 unfolding
+    T = lib()
+    rng = np.random.default_rng(0)
+    dims, ranks = (90, 80), (6, 8)
+    coords = np.stack([rng.integers(0, d, 500) for d in dims]).astype(np.uint32)
+    vals = rng.random(500).astype(np.float32)
+    U0 = [synth.orthonormal_factor(rng, d, r) for d, r in zip(dims, ranks)]
+    ctx = T.tucker_init(dims, coords, vals, ranks, U0)  # allowed: the loss/adjoint works with any ranks
+    with pytest.raises(T.TuckerError) as e:
+        T.hooi_iter(ctx)
+    assert e.value.name == "TUCKER_ERANK"
