@@ -146,6 +146,26 @@ def dist_setup(n_gpus):
     return rank, world, local
 
 
+def time_ttmc_modes(T, torch, ctx, dims, dev, stream, flush, reps=10):
+    """Median CUDA-event duration of ttmc_mode for every mode (L2 flushed before each)."""
+    out = []
+    for n in range(len(dims)):
+        Y = torch.empty((dims[n], ctx.P(n)), dtype=torch.float32, device=dev)
+        T.ttmc_mode(ctx, n, Y, stream=stream)
+        evs = []
+        for i in range(reps):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            T.ttmc_mode(ctx, n, Y, stream=stream)
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        out.append(statistics.median(a.elapsed_time(b) for a, b in evs))
+        del Y
+    return out
+
+
 # ----------------------------------------------------------------------------- reference arm
 def run_reference(args):
     rank, world, _ = dist_setup(args.gpus)
@@ -258,40 +278,13 @@ def run_mine(args):
         phase_ms = [statistics.median(p[i] for p in phase) for i in range(2 * N + 1)]
 
         # TTMc alone, per mode: launch durations with events on the launching stream
-        ttmc_ms = []
-        for n in range(N):
-            Y = torch.empty((w.dims[n], ctx.P(n)), dtype=torch.float32, device=dev)
-            T.ttmc_mode(ctx, n, Y, stream=stream)
-            evs = []
-            for i in range(10):
-                flush.fill_(float(i))
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                T.ttmc_mode(ctx, n, Y, stream=stream)
-                b.record(stream)
-                evs.append((a, b))
-            torch.cuda.synchronize()
-            ttmc_ms.append(statistics.median(a.elapsed_time(b) for a, b in evs))
-            del Y
+        ttmc_ms = time_ttmc_modes(T, torch, ctx, w.dims, dev, stream, flush)
 
         # BF16-factor form on the same workload
-        bf16 = None
+        bf16 = tf32x3 = None
         if not args.no_bf16:
             ctxb = T.tucker_init(w.dims, coords_d, vals_d, w.ranks, U0_d, bf16=True, fit_device=True, stream=stream)
-            bms = []
-            for n in range(N):
-                Y = torch.empty((w.dims[n], ctxb.P(n)), dtype=torch.float32, device=dev)
-                T.ttmc_mode(ctxb, n, Y, stream=stream)
-                evs = []
-                for i in range(10):
-                    flush.fill_(float(i))
-                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    a.record(stream)
-                    T.ttmc_mode(ctxb, n, Y, stream=stream)
-                    b.record(stream)
-                    evs.append((a, b))
-                torch.cuda.synchronize()
-                bms.append(statistics.median(a.elapsed_time(b) for a, b in evs))
+            bms = time_ttmc_modes(T, torch, ctxb, w.dims, dev, stream, flush)
             for _ in range(2):
                 T.hooi_iter(ctxb, fit_buf, stream=stream)
             torch.cuda.synchronize()
@@ -303,8 +296,16 @@ def run_mine(args):
             torch.cuda.synchronize()
             sweep_b = e0.elapsed_time(e1) / 5
             bf16 = {"ttmc_ms_per_mode": bms, "ttmc_nnz_per_s_per_mode": [Zc / (t * 1e-3) for t in bms],
-                    "hooi_s_per_iter": sweep_b * 1e-3, "value": N * Zc / (sweep_b * 1e-3)}
+                    "hooi_s_per_iter": sweep_b * 1e-3, "value": N * Zc / (sweep_b * 1e-3),
+                    "hbm_frac_per_mode": [b_ / (t * 1e-3) / 1e9 / peaks()[0] for b_, t in
+                                          zip([4.0 * N * Zc + 4.0 * w.dims[n] * ctx.P(n) + 4.0 * (w.dims[n] + 1)
+                                               for n in range(N)], bms)]}
             T.tucker_free(ctxb)
+            # opt-in FP32-class form on tensor cores (3xTF32)
+            ctxt = T.tucker_init(w.dims, coords_d, vals_d, w.ranks, U0_d, tf32x3=True, fit_device=True, stream=stream)
+            tms = time_ttmc_modes(T, torch, ctxt, w.dims, dev, stream, flush)
+            tf32x3 = {"ttmc_ms_per_mode": tms, "ttmc_nnz_per_s_per_mode": [Zc / (t * 1e-3) for t in tms]}
+            T.tucker_free(ctxt)
 
     # ---- the differentiation form: loss + adjoint on the completion workload
     adjoint = None
@@ -439,7 +440,7 @@ def run_mine(args):
             "ttmc_nnz_per_s_per_mode": [Zc / (t * 1e-3) for t in ttmc_ms],
             "roofline": dominant, "roofline_other": qrp_roof if dominant is ttmc_roof else ttmc_roof,
             "init_s": init_s, "fit_after_warmup_and_steps": fit,
-            "bf16_factor_form": bf16, "adjoint_form": adjoint, "e2e": e2e, "cpu_baseline": cpu,
+            "bf16_factor_form": bf16, "tf32x3_form": tf32x3, "adjoint_form": adjoint, "e2e": e2e, "cpu_baseline": cpu,
             "clocks": clocks, "gpu_launches": int(launches)}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -56,7 +56,8 @@ typedef enum {
 #define TUCKER_F_QRP_DIRECT 0x2u   /* fat Y_(n) (P_n > I_n): QRP on Y_(n) itself, not on Y Y^T */
 #define TUCKER_F_HOST_INPUT 0x4u   /* coords, vals and U0 given to tucker_init are host pointers */
 #define TUCKER_F_FIT_DEVICE 0x8u   /* hooi_iter writes the fit through a device pointer, no sync */
-#define TUCKER_F_SIMT_TTMC 0x10u   /* TTMc on the FP32 ALUs only (no tensor-core form) */
+#define TUCKER_F_TF32X3 0x10u      /* FP32 form of the TTMc on tensor cores (3xTF32 split: about
+                                      1e-6 relative error instead of FP32 rounding); default off */
 
 /*
  * tucker_init — load a sparse tensor and prepare it for HOOI (Algorithm 2 input:

@@ -1,0 +1,60 @@
+"""The BF16-factor form of the TTMc (factors stored in BF16, tensor-core products,
+FP32 accumulation) against the FP64 oracle: relative Frobenius error <= 1e-2 on
+Y_(n), the bar stated for the BF16 form; and the opt-in tensor-core 3xTF32 form
+against the default FP32 form on the same inputs (2e-6)."""
+import zlib
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2010_10638_gb300 import synth
+from tests.gpu_util import lib, rel_fro, torch
+
+pytestmark = pytest.mark.gpu
+
+CASES = [("order3-r16-zipf", (3000, 2000, 800), (16, 16, 16), 120_000),
+         ("order4-r8", (400, 300, 200, 60), (8, 8, 8, 8), 80_000),
+         ("order3-r16x8", (500, 400, 300), (16, 16, 8), 50_000)]
+
+
+def bf16_round(a):
+    t = torch.as_tensor(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).to(torch.float64)
+    return t.numpy()
+
+
+@pytest.mark.parametrize("name,dims,ranks,nnz", CASES, ids=[c[0] for c in CASES])
+def test_bf16_form_within_1e2(name, dims, ranks, nnz):
+    T = lib()
+    rng = np.random.default_rng(zlib.crc32(name.encode()))
+    coords = np.stack([synth.zipf_indices(rng, d, nnz, 1.1) if "zipf" in name else rng.integers(0, d, nnz)
+                       for d in dims]).astype(np.uint32)
+    vals = rng.lognormal(0.0, 1.0, nnz).astype(np.float32)
+    U = synth.random_factors(rng, dims, ranks)
+    ctx = T.tucker_init(dims, torch.as_tensor(coords.astype(np.int32)).cuda(), torch.as_tensor(vals).cuda(), ranks,
+                        [torch.as_tensor(u).cuda() for u in U], bf16=True)
+    cc, cv = oracle.coalesce(coords, vals.astype(np.float64))
+    Ub = [bf16_round(u) for u in U]
+    Uf = [u.astype(np.float32).astype(np.float64) for u in U]
+    for n in range(len(dims)):
+        Y = T.ttmc_mode(ctx, n).cpu().numpy()
+        err_b = rel_fro(Y, oracle.ttmc(dims, ranks, cc, cv, n, Ub))
+        err_f = rel_fro(Y, oracle.ttmc(dims, ranks, cc, cv, n, Uf))
+        assert err_b <= 1e-2, f"mode {n}: {err_b:.3e} vs BF16-rounded factors"
+        assert err_f <= 1e-2, f"mode {n}: {err_f:.3e} vs FP32 factors"
+
+
+@pytest.mark.parametrize("name,dims,ranks,nnz", CASES, ids=[c[0] for c in CASES])
+def test_tf32x3_form_matches_fp32_form(name, dims, ranks, nnz):
+    T = lib()
+    rng = np.random.default_rng(zlib.crc32(name.encode()) + 1)
+    coords = np.stack([rng.integers(0, d, nnz) for d in dims]).astype(np.uint32)
+    vals = rng.standard_normal(nnz).astype(np.float32)
+    U = synth.random_factors(rng, dims, ranks)
+    args = (dims, torch.as_tensor(coords.astype(np.int32)).cuda(), torch.as_tensor(vals).cuda(), ranks,
+            [torch.as_tensor(u).cuda() for u in U])
+    a = T.tucker_init(*args)
+    b = T.tucker_init(*args, tf32x3=True)
+    for n in range(len(dims)):
+        ya, yb = T.ttmc_mode(a, n), T.ttmc_mode(b, n)
+        assert rel_fro(ya.cpu().numpy(), yb.cpu().numpy()) <= 2e-6
