@@ -375,7 +375,7 @@ __global__ void qrp_q_kernel(QrpArgs a, double *Q, int64_t ldq) {
 // Data written by other blocks during the launch is read with ld.global.cg (L2).
 // Every barrier wait is bounded; on a timeout the kernel records kErrTimeout, fills
 // rdiag with NaN and returns.
-constexpr int kPThreads = 256;
+constexpr int kPThreads = 512;
 constexpr int kPWarps = kPThreads / 32;
 constexpr int kPStage = 2048;  // rows of v staged in shared memory at a time
 constexpr unsigned long long kSpinLimit = 1ull << 25;
@@ -626,8 +626,10 @@ __device__ __forceinline__ double aval(const PArgs &a, int64_t i, int64_t c) {
 }
 
 // argmax of vn over positions [j0, n) in this block's column order (lowest position on
-// ties); swaps it into position j0 of perm_s.  Identical in every block.
-__device__ void pick_pivot(const PArgs &a, int *perm_s, int j0, double *red, int *redi) {
+// ties); swaps it into position j0 of perm_s.  Identical in every block.  Warp-level
+// (value, position) reductions; wred / wredi hold one entry per warp.
+__device__ void pick_pivot(const PArgs &a, int *perm_s, int j0, double *wred, int *wredi) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double best = -1.0;
   int bi = INT_MAX;
   for (int64_t pos = j0 + threadIdx.x; pos < a.n; pos += kPThreads) {
@@ -637,59 +639,90 @@ __device__ void pick_pivot(const PArgs &a, int *perm_s, int j0, double *red, int
       bi = (int)pos;
     }
   }
-  red[threadIdx.x] = best;
-  redi[threadIdx.x] = bi;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double v2 = __shfl_xor_sync(0xffffffffu, best, o);
+    const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (v2 > best || (v2 == best && i2 < bi)) {
+      best = v2;
+      bi = i2;
+    }
+  }
+  if (lane == 0) {
+    wred[warp] = best;
+    wredi[warp] = bi;
+  }
   __syncthreads();
-  for (int o = kPThreads / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) {
-      const double v2 = red[threadIdx.x + o];
-      const int i2 = redi[threadIdx.x + o];
-      if (v2 > red[threadIdx.x] || (v2 == red[threadIdx.x] && i2 < redi[threadIdx.x])) {
-        red[threadIdx.x] = v2;
-        redi[threadIdx.x] = i2;
+  if (warp == 0) {
+    best = lane < kPWarps ? wred[lane] : -1.0;
+    bi = lane < kPWarps ? wredi[lane] : INT_MAX;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double v2 = __shfl_xor_sync(0xffffffffu, best, o);
+      const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (v2 > best || (v2 == best && i2 < bi)) {
+        best = v2;
+        bi = i2;
       }
     }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    const int p = redi[0];
-    if (p != j0 && p < a.n) {
+    if (lane == 0 && bi != j0 && bi < a.n) {
       const int t = perm_s[j0];
-      perm_s[j0] = perm_s[p];
-      perm_s[p] = t;
+      perm_s[j0] = perm_s[bi];
+      perm_s[bi] = t;
     }
   }
   __syncthreads();
+}
+
+// block sum through warp shuffles (fixed order); result in every thread
+__device__ __forceinline__ double block_sum_w(double v, double *wred) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) wred[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+#pragma unroll
+  for (int w = 0; w < kPWarps; ++w) t += wred[w];
+  return t;
 }
 
 template <typename AT>
 __global__ void __launch_bounds__(kPThreads) qrp_persistent_kernel(PArgs a) {
   extern __shared__ __align__(16) unsigned char psm[];
   __shared__ double red[kPThreads];
-  __shared__ int redi[kPThreads];
+  __shared__ double red4[4 * kPThreads];
+  __shared__ double wred[kPWarps];
+  __shared__ int wredi[kPWarps];
+  __shared__ double s_wp[kPWarps][64];  // per-warp partials of V^T y
   __shared__ double s_u[64];
   __shared__ double s_f[64];
+  __shared__ double s_vj[64];
   __shared__ double s_v0, s_tau;
   __shared__ int s_nflag;
   const int64_t n = a.n, m = a.m;
   const int k = a.k;
   int *perm_s = reinterpret_cast<int *>(psm);
   void *stage = psm + ((n * sizeof(int) + 15) & ~(size_t)15);
+  const size_t stage_bytes = max((size_t)kPStage * 8, (size_t)k * k * sizeof(double));
+  double *Ts = reinterpret_cast<double *>(static_cast<unsigned char *>(stage) +
+                                          ((stage_bytes + 15) & ~(size_t)15));  // k x k, this block's T
   const int nb = gridDim.x, b = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t rows_per = (m + nb - 1) / nb;
   const int64_t r0 = min(m, (int64_t)b * rows_per), r1 = min(m, r0 + rows_per);
   const int64_t ld = a.part_ld;
   const int64_t gw = (int64_t)b * kPWarps + warp, nw = (int64_t)nb * kPWarps;
-
-  __shared__ double red4[4 * kPThreads];
   const bool vec4 = sizeof(AT) == 4 && (n % 4) == 0 && (a.lda % 4) == 0 &&
                     (reinterpret_cast<uintptr_t>(a.A) % 16) == 0;
+
   // ---- initial column norms
   if (vec4)
     colsum_rows_f32x4<true>(a, r0, r1, [](int64_t) { return 0.0; }, red4, static_cast<float2 *>(stage));
   else
     colsum_rows<AT, true>(a, r0, r1, [](int64_t) { return 0.0; }, red, stage);
   for (int64_t c = threadIdx.x; c < n; c += kPThreads) perm_s[c] = (int)c;
+  for (int q = threadIdx.x; q < k * k; q += kPThreads) Ts[q] = 0.0;
   if (!grid_sync(a)) return timeout_exit(a);
   for (int64_t c = gw; c < n; c += nw) {
     const double t = warp_part_sum(a, c);
@@ -699,25 +732,27 @@ __global__ void __launch_bounds__(kPThreads) qrp_persistent_kernel(PArgs a) {
       a.flag[c] = 0;
     }
   }
-  if (b == 0)
-    for (int q = threadIdx.x; q < k * k; q += kPThreads) a.T[q] = 0.0;
   if (!grid_sync(a)) return timeout_exit(a);
-  pick_pivot(a, perm_s, 0, red, redi);
+  pick_pivot(a, perm_s, 0, wred, wredi);
 
   const double tol = sqrt(DBL_EPSILON);
   for (int j = 0; j < k; ++j) {
     const int c0 = perm_s[j];
-    // ---- A: pivot column rows
+    // ---- A: pivot column rows y = A[:, c0] - V[:, :j] F[c0, :j]; partials of ||y||^2
+    //      and of V^T y over rows > j (row j enters once v_jj is known)
     if (threadIdx.x < j) s_f[threadIdx.x] = __ldcg(a.F + (int64_t)c0 * k + threadIdx.x);
     __syncthreads();
     double s2 = 0.0;
+    double pl[16];  // V[i, l] * y_i for l < min(j, 16), summed over this thread's rows
+#pragma unroll
+    for (int q = 0; q < 16; ++q) pl[q] = 0.0;
     for (int64_t i = r0 + threadIdx.x; i < r1; i += kPThreads) {
       double y = aval<AT>(a, i, c0);
       const double *vrow = a.V + i * k;
       if ((k & 1) == 0) {  // rows are 16-byte aligned: independent double2 loads
         const double2 *v2 = reinterpret_cast<const double2 *>(vrow);
-        double2 buf[8];
         for (int l0 = 0; l0 < j; l0 += 16) {
+          double2 buf[8];
 #pragma unroll
           for (int q = 0; q < 8; ++q)
             if (l0 + 2 * q < j) buf[q] = __ldcg(v2 + (l0 >> 1) + q);
@@ -734,18 +769,70 @@ __global__ void __launch_bounds__(kPThreads) qrp_persistent_kernel(PArgs a) {
       y = (i >= j) ? y : 0.0;
       s2 = fma(y, y, s2);
       a.V[i * k + j] = y;
+      if (i > j) {  // second pass over the (L1-resident) row: V[i, l] y_i for l < 16
+        if ((k & 1) == 0) {
+          const double2 *v2 = reinterpret_cast<const double2 *>(vrow);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            if (2 * q < j) {
+              const double2 v = __ldcg(v2 + q);
+              pl[2 * q] = fma(v.x, y, pl[2 * q]);
+              if (2 * q + 1 < j) pl[2 * q + 1] = fma(v.y, y, pl[2 * q + 1]);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < 16; ++q)
+            if (q < j) pl[q] = fma(__ldcg(vrow + q), y, pl[q]);
+        }
+      }
     }
-    s2 = block_sum_p(s2, red);
-    if (threadIdx.x == 0) a.part[(int64_t)b * ld + n + k] = s2;
-    if (!grid_sync(a)) return timeout_exit(a);
-    // ---- reflector scalars, identically in every block
+    // ||y||^2 partial and V^T y partials (l < 16 from registers; l >= 16 reloaded)
     {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        if (q < j) {
+          double t = pl[q];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+          if (lane == 0) s_wp[warp][q] = t;
+        }
+      }
+      for (int l = 16; l < j; ++l) {  // same rows as above: each thread reads the y it wrote
+        double t = 0.0;
+        for (int64_t i = r0 + threadIdx.x; i < r1; i += kPThreads)
+          if (i > j) t = fma(__ldcg(a.V + i * k + l), __ldcg(a.V + i * k + j), t);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) s_wp[warp][l] = t;
+      }
+      if (lane == 0) wred[warp] = s2;
+      __syncthreads();
+      if (threadIdx.x < j || threadIdx.x == 63) {
+        const int l = threadIdx.x;
+        double t = 0.0;
+        if (l == 63) {
+          for (int w2 = 0; w2 < kPWarps; ++w2) t += wred[w2];
+          a.part[(int64_t)b * ld + n + k] = t;
+        } else {
+          for (int w2 = 0; w2 < kPWarps; ++w2) t += s_wp[w2][l];
+          a.part[(int64_t)b * ld + n + l] = t;
+        }
+      }
+    }
+    if (!grid_sync(a)) return timeout_exit(a);
+    // ---- reflector scalars, identically in every block (one warp)
+    if (warp == 0) {
+      const double x0 = __ldcg(a.V + (int64_t)j * k + j);
       double t = 0.0;
-      for (int bb = threadIdx.x; bb < nb; bb += kPThreads) t += __ldcg(a.part + (int64_t)bb * ld + n + k);
-      const double a2 = block_sum_p(t, red);
-      if (threadIdx.x == 0) {
-        const double alpha = sqrt(a2);
-        const double x0 = __ldcg(a.V + (int64_t)j * k + j);
+#pragma unroll 4
+      for (int bb = lane; bb < nb; bb += 32) t += __ldcg(a.part + (int64_t)bb * ld + n + k);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) {
+        const double alpha = sqrt(t);
         double tau = 0.0, beta = 0.0, v0 = 0.0;
         if (alpha > 0.0) {
           const double sg = (x0 < 0.0) ? -1.0 : 1.0;
@@ -761,57 +848,57 @@ __global__ void __launch_bounds__(kPThreads) qrp_persistent_kernel(PArgs a) {
           a.nflag[j] = 0;
         }
       }
-      __syncthreads();
     }
+    __syncthreads();
     const double v0 = s_v0, tau = s_tau;
-    // ---- B: A^T v_j and V^T v_j over this block's rows (v_j is zero above row j)
+    // ---- B: A^T v_j over this block's rows (v_j is zero above row j)
     const int64_t rb0 = max(r0, (int64_t)j);
     auto vfun = [&](int64_t i) { return (i == j) ? v0 : __ldcg(a.V + i * k + j); };
     if (vec4)
       colsum_rows_f32x4<false>(a, rb0, max(rb0, r1), vfun, red4, static_cast<float2 *>(stage));
     else
       colsum_rows<AT, false>(a, rb0, max(rb0, r1), vfun, red, stage);
-    for (int l = warp; l < j; l += kPWarps) {
-      double t = 0.0;
-      for (int64_t i = rb0 + lane; i < r1; i += 32) t = fma(__ldcg(a.V + i * k + l), vfun(i), t);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      if (lane == 0) a.part[(int64_t)b * ld + n + l] = t;
-    }
     if (!grid_sync(a)) return timeout_exit(a);
-    // ---- C: F[:, j], row j of R, norm downdate
+    // ---- C: u = V^T v_j, this block's T, then F[:, j], row j of R, norm downdate
     // Row j of V gets v_jj only now: every block read x0 from it between the first two
     // barriers of this step, and until then only its owner used v_jj (from s_v0).
     if (threadIdx.x == 0 && j >= r0 && j < r1) a.V[(int64_t)j * k + j] = v0;
-    const bool has_cols = (int64_t)j + 1 + (int64_t)b * kPWarps < n;
-    if (has_cols || b == 0) {
+    {
+      const double vj = (threadIdx.x < j) ? __ldcg(a.V + (int64_t)j * k + threadIdx.x) : 0.0;
       for (int l = warp; l < j; l += kPWarps) {
         const double t = warp_part_sum(a, n + l);
         if (lane == 0) s_u[l] = t;
       }
+      if (threadIdx.x < j) s_vj[threadIdx.x] = vj;
       __syncthreads();
-    }
-    if (b == 0) {
-      for (int l = threadIdx.x; l < j; l += kPThreads) {
+      if (threadIdx.x < j) s_u[threadIdx.x] = fma(s_vj[threadIdx.x], v0, s_u[threadIdx.x]);  // + V[j, l] v_jj
+      __syncthreads();
+      // T(0:j, j) = -tau T(0:j, 0:j) u, T(j, j) = tau
+      if (threadIdx.x < j) {
+        const int l = threadIdx.x;
         double t = 0.0;
-        for (int q = l; q < j; ++q) t = fma(__ldcg(a.T + (int64_t)l * k + q), s_u[q], t);
-        a.T[(int64_t)l * k + j] = -tau * t;
+        for (int q = l; q < j; ++q) t = fma(Ts[l * k + q], s_u[q], t);
+        Ts[l * k + j] = -tau * t;
       }
-      if (threadIdx.x == 0) a.T[(int64_t)j * k + j] = tau;
-    }
-    if (has_cols) {
-      if (threadIdx.x < j) s_f[threadIdx.x] = __ldcg(a.V + (int64_t)j * k + threadIdx.x);  // row j of V
-      __syncthreads();
+      if (threadIdx.x == 0) Ts[j * k + j] = tau;
     }
     for (int64_t pos = j + 1 + gw; pos < n; pos += nw) {
       const int c = perm_s[pos];
-      const double w = warp_part_sum(a, c);
       const double *frow = a.F + (int64_t)c * k;
+      // every load of this column first (one round trip), then the arithmetic
+      const double f0 = (lane < j) ? __ldcg(frow + lane) : 0.0;
+      const double f1 = (lane + 32 < j) ? __ldcg(frow + lane + 32) : 0.0;
+      const double ajc = aval<AT>(a, j, c);
+      const double vnc = __ldcg(a.vn + c), ref = __ldcg(a.vref + c);
+      const double w = warp_part_sum(a, c);
       double corr = 0.0, rv = 0.0;
-      for (int l = lane; l < j; l += 32) {
-        const double fl = __ldcg(frow + l);
-        corr = fma(fl, s_u[l], corr);
-        rv = fma(s_f[l], fl, rv);
+      if (lane < j) {
+        corr = f0 * s_u[lane];
+        rv = s_vj[lane] * f0;
+      }
+      if (lane + 32 < j) {
+        corr = fma(f1, s_u[lane + 32], corr);
+        rv = fma(s_vj[lane + 32], f1, rv);
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -821,10 +908,9 @@ __global__ void __launch_bounds__(kPThreads) qrp_persistent_kernel(PArgs a) {
       if (lane == 0) {
         const double f = tau * (w - corr);
         a.F[(int64_t)c * k + j] = f;
-        double r = aval<AT>(a, j, c) - rv;
+        double r = ajc - rv;
         r = fma(-v0, f, r);
-        double nv = __ldcg(a.vn + c) - r * r;
-        const double ref = __ldcg(a.vref + c);
+        double nv = vnc - r * r;
         if (ref > 0.0 && !(nv > tol * ref)) {
           a.flag[c] = 1;
           atomicAdd(a.nflag + j, 1);
@@ -849,7 +935,7 @@ __global__ void __launch_bounds__(kPThreads) qrp_persistent_kernel(PArgs a) {
           for (int l = 0; l <= j; ++l) y = fma(-__ldcg(a.V + i * k + l), __ldcg(a.F + (int64_t)c * k + l), y);
           t = fma(y, y, t);
         }
-        t = block_sum_p(t, red);
+        t = block_sum_w(t, wred);
         if (threadIdx.x == 0) a.part[(int64_t)b * ld + c] = t;
       }
       if (!grid_sync(a)) return timeout_exit(a);
@@ -865,15 +951,16 @@ __global__ void __launch_bounds__(kPThreads) qrp_persistent_kernel(PArgs a) {
       }
       if (!grid_sync(a)) return timeout_exit(a);
     }
-    if (j + 1 < k) pick_pivot(a, perm_s, j + 1, red, redi);
+    if (j + 1 < k) pick_pivot(a, perm_s, j + 1, wred, wredi);
   }
 
-  // ---- Q = [I_k; 0] - V (T V[0:k, :]^T), rows of this block
+  // ---- Q = [I_k; 0] - V (T V[0:k, :]^T), rows of this block (T from this block's copy)
   double *Ms = reinterpret_cast<double *>(stage);
+  __syncthreads();
   for (int q = threadIdx.x; q < k * k; q += kPThreads) {
     const int l = q / k, cc = q % k;
     double t = 0.0;
-    for (int p = l; p <= cc; ++p) t = fma(__ldcg(a.T + (int64_t)l * k + p), __ldcg(a.V + (int64_t)cc * k + p), t);
+    for (int p = l; p <= cc; ++p) t = fma(Ts[l * k + p], __ldcg(a.V + (int64_t)cc * k + p), t);
     Ms[q] = t;
   }
   __syncthreads();
@@ -897,15 +984,14 @@ static bool qrp_persistent(const AT *A, int64_t m, int64_t n, int64_t lda, int k
   if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return false;
   const size_t perm_bytes = ((size_t)n * sizeof(int) + 15) & ~(size_t)15;
   const size_t stage_bytes = std::max<size_t>((size_t)kPStage * 8, (size_t)k * k * sizeof(double));
-  const size_t smem = perm_bytes + stage_bytes;
+  const size_t smem = perm_bytes + ((stage_bytes + 15) & ~(size_t)15) + (size_t)k * k * sizeof(double);
   auto kern = qrp_persistent_kernel<AT>;
-  if (smem > 48 * 1024 &&
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return false;
+  // the 48 KB default bounds static + dynamic shared memory together: always opt in
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return false;
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPThreads, smem) != cudaSuccess || per_sm < 1)
     return false;
-  int64_t nb = std::min<int64_t>((int64_t)per_sm * nb_sms, 2 * (int64_t)nb_sms);
+  int64_t nb = std::min<int64_t>((int64_t)per_sm * nb_sms, (int64_t)nb_sms);
   nb = std::min<int64_t>(nb, std::max<int64_t>(1, (m * std::max<int64_t>(n, 1)) / 8192));
   nb = std::max<int64_t>(1, std::min<int64_t>(nb, m));
   PArgs a{};

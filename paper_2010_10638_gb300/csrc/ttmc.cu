@@ -258,6 +258,141 @@ __global__ void __launch_bounds__(kTtmcWarps * 32) ttmc_fast_kernel(const TtmcPa
   }
 }
 
+// ============================================================================ pipelined form
+// The arithmetic of ttmc_fast_kernel (order 3: one left mode) with the global latency of
+// each tile shortened: the slice offsets, indices and values of tile t+1 are loaded into
+// registers while tile t is staged and computed, so a tile waits on one round trip (the
+// L1-cached factor-row gathers) instead of three chained ones.
+template <int PL, int RB, int TA, int TB>
+__global__ void __launch_bounds__(kTtmcWarps * 32) ttmc_pipe_kernel(const TtmcParams p) {
+  constexpr int G = (PL / TA) * (RB / TB);
+  constexpr int NG = 32 / G;
+  static_assert(G * NG == 32, "group size must divide the warp");
+  static_assert(PL % 4 == 0 && RB % 4 == 0, "16-byte row pieces");
+  extern __shared__ float4 smem_f4[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float *xa = reinterpret_cast<float *>(smem_f4) + w * 32 * (PL + RB);
+  float *bb = xa + 32 * PL;
+  const int64_t u = (int64_t)blockIdx.x * kTtmcWarps + w;
+  if (u >= p.n_units) return;
+  const float *UA = static_cast<const float *>(p.U[0]);
+  const float *UB = static_cast<const float *>(p.U[1]);
+  const uint32_t *idxA = p.idx[0];
+  const uint32_t *idxB = p.idx[1];
+  const uint32_t e0 = __ldg(p.unit_e0 + u);
+  const uint32_t e_end = (u + 1 < p.n_units) ? __ldg(p.unit_e0 + u + 1) : p.Z;
+  const int slot = __ldg(p.unit_slot + u);
+  const int ntiles = (int)((e_end - e0 + 31u) / 32u);
+  const int g = lane / G, j = lane % G;
+  const int ra0 = (j / (RB / TB)) * TA, rb0 = (j % (RB / TB)) * TB;
+  float acc[TA][TB];
+#pragma unroll
+  for (int a = 0; a < TA; ++a)
+#pragma unroll
+    for (int b = 0; b < TB; ++b) acc[a][b] = 0.f;
+
+  uint32_t kb = __ldg(p.unit_k0 + u);
+  uint32_t bound = (kb + 1u + lane <= p.S) ? __ldg(p.sptr + kb + 1u + lane) : 0xffffffffu;
+  float x = 0.f;
+  uint32_t ia = 0u, ib = 0u;
+  if (e0 + lane < e_end) {
+    x = __ldg(p.val + e0 + lane);
+    ia = __ldg(idxA + e0 + lane);
+    ib = __ldg(idxB + e0 + lane);
+  }
+  for (int t = 0; t < ntiles; ++t) {
+    const uint32_t e = e0 + 32u * (uint32_t)t;
+    const int nt = (int)min(32u, e_end - e);
+    const uint32_t q = bound - e;
+    uint32_t starts = __reduce_or_sync(kFull, q < 32u ? (1u << q) : 0u);
+    starts &= (nt >= 32) ? kFull : ((1u << nt) - 1u);
+    const uint32_t kp = kb + __popc(starts & ((2u << lane) - 1u));
+    const bool end_is_start = __any_sync(kFull, q == (uint32_t)nt);
+    const uint32_t kb_next = kb + __popc(__ballot_sync(kFull, q <= (uint32_t)nt));
+    // loads of tile t+1 (consumed next iteration)
+    const uint32_t bound_next = (kb_next + 1u + lane <= p.S) ? __ldg(p.sptr + kb_next + 1u + lane) : 0xffffffffu;
+    float xn = 0.f;
+    uint32_t ian = 0u, ibn = 0u;
+    const uint32_t posn = e + 32u + (uint32_t)lane;
+    if (posn < e_end) {
+      xn = __ldg(p.val + posn);
+      ian = __ldg(idxA + posn);
+      ibn = __ldg(idxB + posn);
+    }
+    // stage tile t: x * left rows, last-mode rows
+#pragma unroll
+    for (int it = lane; it < 32 * (PL / 4); it += 32) {
+      const int tt = it / (PL / 4), c = (it % (PL / 4)) * 4;
+      const float xt = __shfl_sync(kFull, x, tt);
+      const uint32_t r = __shfl_sync(kFull, ia, tt);
+      float4 v = __ldg(reinterpret_cast<const float4 *>(UA + (size_t)r * PL + c));
+      v.x *= xt;
+      v.y *= xt;
+      v.z *= xt;
+      v.w *= xt;
+      *reinterpret_cast<float4 *>(xa + tt * PL + c) = v;
+    }
+#pragma unroll
+    for (int it = lane; it < 32 * (RB / 4); it += 32) {
+      const int tt = it / (RB / 4), c = (it % (RB / 4)) * 4;
+      const uint32_t r = __shfl_sync(kFull, ib, tt);
+      *reinterpret_cast<float4 *>(bb + tt * RB + c) = __ldg(reinterpret_cast<const float4 *>(UB + (size_t)r * RB + c));
+    }
+    __syncwarp();
+    uint32_t segs = starts | 1u;
+    while (segs) {
+      const int p0 = __ffs(segs) - 1;
+      segs &= segs - 1u;
+      const int p1 = segs ? (__ffs(segs) - 1) : nt;
+      int qq = p0 + g;
+      auto step = [&](int r) {
+        float av[TA], bv[TB];
+        lds<TA>(xa + r * PL + ra0, av);
+        lds<TB>(bb + r * RB + rb0, bv);
+#pragma unroll
+        for (int a = 0; a < TA; ++a)
+#pragma unroll
+          for (int b = 0; b < TB; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+      };
+      for (; qq + NG < p1; qq += 2 * NG) {
+        step(qq);
+        step(qq + NG);
+      }
+      if (qq < p1) step(qq);
+      const bool flush = (p1 < nt) || end_is_start || (e + (uint32_t)nt == e_end);
+      if (flush) {
+#pragma unroll
+        for (int o = G; o < 32; o <<= 1)
+#pragma unroll
+          for (int a = 0; a < TA; ++a)
+#pragma unroll
+            for (int b = 0; b < TB; ++b) acc[a][b] += __shfl_xor_sync(kFull, acc[a][b], o);
+        const uint32_t kseg = __shfl_sync(kFull, kp, p0);
+        if (g == 0) {
+          float *dst = (slot >= 0) ? p.carry + (size_t)slot * p.P : p.Y + (size_t)__ldg(p.sid + kseg) * p.P;
+#pragma unroll
+          for (int a = 0; a < TA; ++a) {
+            float *d = dst + (size_t)(ra0 + a) * RB + rb0;
+#pragma unroll
+            for (int b = 0; b < TB; b += 4)
+              *reinterpret_cast<float4 *>(d + b) = make_float4(acc[a][b], acc[a][b + 1], acc[a][b + 2], acc[a][b + 3]);
+          }
+        }
+#pragma unroll
+        for (int a = 0; a < TA; ++a)
+#pragma unroll
+          for (int b = 0; b < TB; ++b) acc[a][b] = 0.f;
+      }
+    }
+    __syncwarp();
+    kb = kb_next;
+    bound = bound_next;
+    x = xn;
+    ia = ian;
+    ib = ibn;
+  }
+}
+
 // ============================================================================ tensor-core form
 // The contribution of one slice is the small GEMM  Y_i (PL x RB) = A_i^T B_i  with
 // A_i = [x_z a_z] and B_i = [b_z] over its nonzeros z (K = slice length).  PL = 16 k
@@ -298,6 +433,193 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], 
 }
 
 __host__ __device__ constexpr int stride_mod32_8(int v) { return v + ((8 - (v % 32)) % 32 + 32) % 32; }
+
+// BF16-factor form with ldmatrix fragments.  Staging (lane = nonzero of the tile): the
+// left Kronecker row times x_z is formed in FP32 from the BF16 factor rows and rounded to
+// BF16; the last-mode row is copied as is.  Both are stored k-major ([nonzero][rank],
+// 48-byte or 16-byte-multiple padded rows), so that ldmatrix .trans hands each lane its
+// m16n8k16 A and B fragments directly; nonzeros outside the current slice segment are
+// masked in the A fragment (BF16 halves zeroed).  Slice offsets, indices and values of
+// tile t+1 are prefetched into registers while tile t is processed.
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t (&r)[4], const void *row_addr) {
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(row_addr);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(sa));
+}
+__device__ __forceinline__ void ldsm_x2_trans(uint32_t &r0, uint32_t &r1, const void *row_addr) {
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(row_addr);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(sa));
+}
+__host__ __device__ constexpr int bf16_stride(int v) {  // row stride (elements): 16-byte rows, 16 (mod 64) bytes
+  return ((v * 2 + 15) / 16 * 16 % 128 == 16 || (v * 2 + 15) / 16 * 16 % 128 == 48 ||
+          (v * 2 + 15) / 16 * 16 % 128 == 80 || (v * 2 + 15) / 16 * 16 % 128 == 112)
+             ? (v * 2 + 15) / 16 * 8
+             : (v * 2 + 15) / 16 * 8 + 8;
+}
+
+template <int NL, int PL, int RB>
+__global__ void __launch_bounds__(kTtmcWarps * 32) ttmc_bf16_kernel(const TtmcParams p) {
+  static_assert(PL % 16 == 0 && RB % 8 == 0, "mma tiles");
+  constexpr int MT = PL / 16, NT = RB / 8;
+  constexpr int SA = bf16_stride(PL), SB = bf16_stride(RB);  // in BF16 elements
+  constexpr int ROWS = 48;                                   // 32 nonzeros + a 16-row zero tail
+  extern __shared__ float4 smem_f4[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __nv_bfloat16 *As = reinterpret_cast<__nv_bfloat16 *>(smem_f4) + (size_t)w * ROWS * (SA + SB);
+  __nv_bfloat16 *Bs = As + ROWS * SA;
+  const int64_t u = (int64_t)blockIdx.x * kTtmcWarps + w;
+  if (u >= p.n_units) return;
+  const __nv_bfloat16 *UA0 = static_cast<const __nv_bfloat16 *>(p.U[0]);
+  const __nv_bfloat16 *UA1 = static_cast<const __nv_bfloat16 *>(p.U[1]);
+  const __nv_bfloat16 *UB = static_cast<const __nv_bfloat16 *>(p.U[NL]);
+  const uint32_t e0 = __ldg(p.unit_e0 + u);
+  const uint32_t e_end = (u + 1 < p.n_units) ? __ldg(p.unit_e0 + u + 1) : p.Z;
+  const int slot = __ldg(p.unit_slot + u);
+  const int ntiles = (int)((e_end - e0 + 31u) / 32u);
+  const int g = lane >> 2, t4 = lane & 3;
+  for (int q = lane; q < 16 * SA; q += 32) As[32 * SA + q] = __float2bfloat16(0.f);
+  for (int q = lane; q < 16 * SB; q += 32) Bs[32 * SB + q] = __float2bfloat16(0.f);
+  float acc[MT][NT][4];
+#pragma unroll
+  for (int i = 0; i < MT; ++i)
+#pragma unroll
+    for (int jn = 0; jn < NT; ++jn)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[i][jn][q] = 0.f;
+
+  uint32_t kb = __ldg(p.unit_k0 + u);
+  uint32_t bound = (kb + 1u + lane <= p.S) ? __ldg(p.sptr + kb + 1u + lane) : 0xffffffffu;
+  float x = 0.f;
+  uint32_t i0 = 0u, i1 = 0u, ib = 0u;
+  if (e0 + lane < e_end) {
+    x = __ldg(p.val + e0 + lane);
+    i0 = __ldg(p.idx[0] + e0 + lane);
+    if constexpr (NL == 2) i1 = __ldg(p.idx[1] + e0 + lane);
+    ib = __ldg(p.idx[NL] + e0 + lane);
+  }
+  for (int t = 0; t < ntiles; ++t) {
+    const uint32_t e = e0 + 32u * (uint32_t)t;
+    const int nt = (int)min(32u, e_end - e);
+    const uint32_t q = bound - e;
+    uint32_t starts = __reduce_or_sync(kFull, q < 32u ? (1u << q) : 0u);
+    starts &= (nt >= 32) ? kFull : ((1u << nt) - 1u);
+    const uint32_t kp = kb + __popc(starts & ((2u << lane) - 1u));
+    const bool end_is_start = __any_sync(kFull, q == (uint32_t)nt);
+    const uint32_t kb_next = kb + __popc(__ballot_sync(kFull, q <= (uint32_t)nt));
+    const uint32_t bound_next = (kb_next + 1u + lane <= p.S) ? __ldg(p.sptr + kb_next + 1u + lane) : 0xffffffffu;
+    float xn = 0.f;
+    uint32_t i0n = 0u, i1n = 0u, ibn = 0u;
+    const uint32_t posn = e + 32u + (uint32_t)lane;
+    if (posn < e_end) {
+      xn = __ldg(p.val + posn);
+      i0n = __ldg(p.idx[0] + posn);
+      if constexpr (NL == 2) i1n = __ldg(p.idx[1] + posn);
+      ibn = __ldg(p.idx[NL] + posn);
+    }
+    // ---- staging: row `lane` of the tile
+    {
+      __nv_bfloat16 *arow = As + lane * SA;
+      if constexpr (NL == 1) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(UA0 + (size_t)i0 * PL);
+#pragma unroll
+        for (int c = 0; c < PL / 8; ++c) {
+          uint4 v = __ldg(src + c);
+          __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(&v);
+#pragma unroll
+          for (int qq = 0; qq < 4; ++qq) {
+            const float2 f = __bfloat1622float2(h[qq]);
+            h[qq] = __floats2bfloat162_rn(f.x * x, f.y * x);
+          }
+          *reinterpret_cast<uint4 *>(arow + 8 * c) = v;
+        }
+      } else {
+        const int R0 = p.R[0], R1 = p.R[1];
+        const __nv_bfloat16 *ra = UA0 + (size_t)i0 * R0;
+        const __nv_bfloat16 *rb = UA1 + (size_t)i1 * R1;
+        for (int a0 = 0; a0 < R0; ++a0) {
+          const float s0 = x * __bfloat162float(ra[a0]);
+          for (int a1 = 0; a1 < R1; a1 += 2) {
+            const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(rb + a1));
+            *reinterpret_cast<__nv_bfloat162 *>(arow + a0 * R1 + a1) = __floats2bfloat162_rn(s0 * f.x, s0 * f.y);
+          }
+        }
+      }
+      const uint4 *srcb = reinterpret_cast<const uint4 *>(UB + (size_t)ib * RB);
+      __nv_bfloat16 *brow = Bs + lane * SB;
+#pragma unroll
+      for (int c = 0; c < RB / 8; ++c) *reinterpret_cast<uint4 *>(brow + 8 * c) = __ldg(srcb + c);
+    }
+    __syncwarp();
+    uint32_t segs = starts | 1u;
+    while (segs) {
+      const int p0 = __ffs(segs) - 1;
+      segs &= segs - 1u;
+      const int p1 = segs ? (__ffs(segs) - 1) : nt;
+      for (int ks = p0; ks < p1; ks += 16) {
+        // masks of the BF16 halves by nonzero index: k = ks + 2 t4 (+1), ks + 8 + 2 t4 (+1)
+        const int k0 = ks + 2 * t4, k8 = k0 + 8;
+        const uint32_t m0 = (k0 < p1 ? 0x0000ffffu : 0u) | (k0 + 1 < p1 ? 0xffff0000u : 0u);
+        const uint32_t m8 = (k8 < p1 ? 0x0000ffffu : 0u) | (k8 + 1 < p1 ? 0xffff0000u : 0u);
+        const int mrow = lane & 7, msel = lane >> 3;  // ldmatrix: lanes 8j..8j+7 address matrix j
+        uint32_t bfr[NT][2];
+#pragma unroll
+        for (int nq = 0; nq < NT; nq += 2) {
+          if (nq + 1 < NT) {
+            // matrices: (k 0-7, n nq*8), (k 8-15, n nq*8), (k 0-7, n nq*8+8), (k 8-15, n nq*8+8)
+            const int kr = ks + mrow + ((msel & 1) ? 8 : 0);
+            const int nc = nq * 8 + ((msel & 2) ? 8 : 0);
+            uint32_t r[4];
+            ldsm_x4_trans(r, Bs + kr * SB + nc);
+            bfr[nq][0] = r[0];
+            bfr[nq][1] = r[1];
+            bfr[nq + 1][0] = r[2];
+            bfr[nq + 1][1] = r[3];
+          } else {
+            const int kr = ks + mrow + ((msel & 1) ? 8 : 0);
+            ldsm_x2_trans(bfr[nq][0], bfr[nq][1], Bs + kr * SB + nq * 8);
+          }
+        }
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) {
+          // matrices: (k 0-7, m), (k 0-7, m+8), (k 8-15, m), (k 8-15, m+8) -> a0 a1 a2 a3
+          const int kr = ks + mrow + ((msel & 2) ? 8 : 0);
+          const int mc = mt * 16 + ((msel & 1) ? 8 : 0);
+          uint32_t a[4];
+          ldsm_x4_trans(a, As + kr * SA + mc);
+          a[0] &= m0;
+          a[1] &= m0;
+          a[2] &= m8;
+          a[3] &= m8;
+#pragma unroll
+          for (int nq = 0; nq < NT; ++nq) mma_bf16(acc[mt][nq], a, bfr[nq][0], bfr[nq][1]);
+        }
+      }
+      const bool flush = (p1 < nt) || end_is_start || (e + (uint32_t)nt == e_end);
+      if (flush) {
+        const uint32_t kseg = __shfl_sync(kFull, kp, p0);
+        float *dst = (slot >= 0) ? p.carry + (size_t)slot * p.P : p.Y + (size_t)__ldg(p.sid + kseg) * p.P;
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+          for (int nq = 0; nq < NT; ++nq) {
+            const int row = mt * 16 + g, col = nq * 8 + 2 * t4;
+            *reinterpret_cast<float2 *>(dst + (size_t)row * RB + col) = make_float2(acc[mt][nq][0], acc[mt][nq][1]);
+            *reinterpret_cast<float2 *>(dst + (size_t)(row + 8) * RB + col) =
+                make_float2(acc[mt][nq][2], acc[mt][nq][3]);
+            acc[mt][nq][0] = acc[mt][nq][1] = acc[mt][nq][2] = acc[mt][nq][3] = 0.f;
+          }
+      }
+    }
+    __syncwarp();
+    kb = kb_next;
+    bound = bound_next;
+    x = xn;
+    i0 = i0n;
+    i1 = i1n;
+    ib = ibn;
+  }
+}
 
 template <int NL, int PL, int RB, int MODE, typename FT>
 __global__ void __launch_bounds__(kTtmcWarps * 32) ttmc_mma_kernel(const TtmcParams p) {
@@ -569,8 +891,21 @@ static cudaError_t run_fast(const TtmcParams &p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <int NL, int PL, int RB>
+static cudaError_t run_bf16(const TtmcParams &p, cudaStream_t s) {
+  const size_t smem = (size_t)kTtmcWarps * 48 * (bf16_stride(PL) + bf16_stride(RB)) * sizeof(__nv_bfloat16);
+  auto kern = ttmc_bf16_kernel<NL, PL, RB>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const unsigned blocks = (unsigned)((p.n_units + kTtmcWarps - 1) / kTtmcWarps);
+  kern<<<blocks, kTtmcWarps * 32, smem, s>>>(p);
+  ::tk::count_launch();
+  return cudaGetLastError();
+}
+
 template <int NL, int PL, int RB, int MODE, typename FT>
 static cudaError_t run_mma(const TtmcParams &p, cudaStream_t s) {
+  if constexpr (MODE == kBf16) return run_bf16<NL, PL, RB>(p, s);
   constexpr int KS = (MODE == kTf32x3) ? 8 : 16;
   const size_t smem =
       (size_t)kTtmcWarps * (32 + KS) * (stride_mod32_8(PL) + stride_mod32_8(RB)) * sizeof(float);
@@ -606,6 +941,36 @@ static bool dispatch_mma(const TtmcParams &p, cudaStream_t s, cudaError_t *err) 
     if (PL == 64 && RB == 16) TK_MMA(2, 64, 16)
   }
 #undef TK_MMA
+  return false;
+}
+
+template <int PL, int RB, int TA, int TB>
+static cudaError_t run_pipe(const TtmcParams &p, cudaStream_t s) {
+  const size_t smem = (size_t)kTtmcWarps * 32 * (PL + RB) * sizeof(float);
+  auto kern = ttmc_pipe_kernel<PL, RB, TA, TB>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const unsigned blocks = (unsigned)((p.n_units + kTtmcWarps - 1) / kTtmcWarps);
+  kern<<<blocks, kTtmcWarps * 32, smem, s>>>(p);
+  ::tk::count_launch();
+  return cudaGetLastError();
+}
+
+// Pipelined FP32 dispatch (order 3, row-aligned factors).
+static bool dispatch_pipe(const TtmcParams &p, cudaStream_t s, cudaError_t *err) {
+  if (p.nother != 2) return false;
+  const int PL = p.R[0], RB = p.R[1];
+#define TK_PIPE(PL_, RB_, TA_, TB_)                   \
+  {                                                   \
+    *err = run_pipe<PL_, RB_, TA_, TB_>(p, s);        \
+    return true;                                      \
+  }
+  if (PL == 16 && RB == 16) TK_PIPE(16, 16, 4, 4)
+  if (PL == 8 && RB == 8) TK_PIPE(8, 8, 2, 4)
+  if (PL == 32 && RB == 32) TK_PIPE(32, 32, 8, 4)
+  if (PL == 16 && RB == 8) TK_PIPE(16, 8, 4, 4)
+  if (PL == 8 && RB == 16) TK_PIPE(8, 16, 4, 4)
+#undef TK_PIPE
   return false;
 }
 
@@ -684,6 +1049,8 @@ static tucker_status ttmc_impl(Ctx *c, int mode, float *Y, const float *val, con
       done = dispatch_mma<kBf16, __nv_bfloat16>(p, s, &err);
     else if (c->flags & TUCKER_F_TF32X3)  // opt-in FP32-class form on the tensor cores
       done = dispatch_mma<kTf32x3, float>(p, s, &err);
+    else if (!(c->flags & TUCKER_F_UNPIPELINED))
+      done = dispatch_pipe(p, s, &err);
     if (!done) done = bf16 ? dispatch_fast<__nv_bfloat16>(p, s, &err) : dispatch_fast<float>(p, s, &err);
     if (!done) err = bf16 ? run_generic<__nv_bfloat16>(p, s) : run_generic<float>(p, s);
     TK_CUDA(err);

@@ -28,6 +28,7 @@ TUCKER_F_QRP_DIRECT = 0x2
 TUCKER_F_HOST_INPUT = 0x4
 TUCKER_F_FIT_DEVICE = 0x8
 TUCKER_F_TF32X3 = 0x10
+TUCKER_F_UNPIPELINED = 0x20
 
 STATUS = {0: "TUCKER_OK", 1: "TUCKER_EINVAL", 2: "TUCKER_ERANK", 3: "TUCKER_ENOMEM", 4: "TUCKER_ECUDA",
           5: "TUCKER_ETIMEOUT", 6: "TUCKER_ESTATE"}
@@ -145,14 +146,16 @@ class Context:
 
 # --------------------------------------------------------------------------- entry points
 def tucker_init(dims, coords, vals, ranks, U0=None, seed: int = 0, bf16: bool = False, direct: bool = False,
-                fit_device: bool = False, tf32x3: bool = False, stream=None) -> Context:
+                fit_device: bool = False, tf32x3: bool = False, unpipelined: bool = False,
+                stream=None) -> Context:
     """coords: int32/uint32 [N, nnz]; vals: float32 [nnz]; U0: list of N float64 [I_m, R_m] or None.
     CUDA tensors are passed as device pointers; CPU tensors / numpy arrays as host pointers
     (TUCKER_F_HOST_INPUT; all inputs must then be on the host)."""
     lib = load()
     N = len(dims)
     flags = (TUCKER_F_BF16_FACTORS if bf16 else 0) | (TUCKER_F_QRP_DIRECT if direct else 0) | (
-        TUCKER_F_FIT_DEVICE if fit_device else 0) | (TUCKER_F_TF32X3 if tf32x3 else 0)
+        TUCKER_F_FIT_DEVICE if fit_device else 0) | (TUCKER_F_TF32X3 if tf32x3 else 0) | (
+        TUCKER_F_UNPIPELINED if unpipelined else 0)
     on_host = not (isinstance(coords, torch.Tensor) and coords.is_cuda)
     keep = []
     if on_host:

@@ -78,3 +78,18 @@ def test_qrp_rejects_bad_sizes():
     with pytest.raises(T.TuckerError):
         T.qrp_leading(torch.zeros((3, 5), dtype=torch.float64, device="cuda"), 2,
                       work=torch.empty(64, dtype=torch.uint8, device="cuda"))
+
+
+def test_qrp_runs_as_one_persistent_launch():
+    """Factorisations with n <= 8192 run as one cooperative launch (the multi-kernel
+    form, kept for wider matrices, launches 3k + 3 kernels)."""
+    T = lib()
+    rng = np.random.default_rng(5)
+    for m, n, k in [(50_000, 256, 16), (1000, 256, 16), (40, 6, 4)]:
+        A = torch.as_tensor(rng.standard_normal((m, n))).cuda()
+        T.qrp_leading(A, k)  # warm-up (first-use attribute set-up)
+        torch.cuda.synchronize()
+        before = T.tucker_kernel_launches()
+        T.qrp_leading(A, k)
+        torch.cuda.synchronize()
+        assert T.tucker_kernel_launches() - before == 1, (m, n, k)
