@@ -517,23 +517,27 @@ __global__ void __launch_bounds__(kTtmcWarps * 32) ttmc_bf16_kernel(const TtmcPa
       if constexpr (NL == 2) i1n = __ldg(p.idx[1] + posn);
       ibn = __ldg(p.idx[NL] + posn);
     }
-    // ---- staging: row `lane` of the tile
+    // ---- staging.  16-byte pieces: consecutive lanes take consecutive pieces of one row,
+    // so a row's pieces share one L1 request.
     {
-      __nv_bfloat16 *arow = As + lane * SA;
       if constexpr (NL == 1) {
-        const uint4 *src = reinterpret_cast<const uint4 *>(UA0 + (size_t)i0 * PL);
+        constexpr int PA = PL / 8;  // pieces per row
 #pragma unroll
-        for (int c = 0; c < PL / 8; ++c) {
-          uint4 v = __ldg(src + c);
+        for (int it = lane; it < 32 * PA; it += 32) {
+          const int tt = it / PA, c = it % PA;
+          const float xt = __shfl_sync(kFull, x, tt);
+          const uint32_t r = __shfl_sync(kFull, i0, tt);
+          uint4 v = __ldg(reinterpret_cast<const uint4 *>(UA0 + (size_t)r * PL) + c);
           __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(&v);
 #pragma unroll
           for (int qq = 0; qq < 4; ++qq) {
             const float2 f = __bfloat1622float2(h[qq]);
-            h[qq] = __floats2bfloat162_rn(f.x * x, f.y * x);
+            h[qq] = __floats2bfloat162_rn(f.x * xt, f.y * xt);
           }
-          *reinterpret_cast<uint4 *>(arow + 8 * c) = v;
+          *reinterpret_cast<uint4 *>(As + tt * SA + 8 * c) = v;
         }
       } else {
+        __nv_bfloat16 *arow = As + lane * SA;
         const int R0 = p.R[0], R1 = p.R[1];
         const __nv_bfloat16 *ra = UA0 + (size_t)i0 * R0;
         const __nv_bfloat16 *rb = UA1 + (size_t)i1 * R1;
@@ -545,10 +549,13 @@ __global__ void __launch_bounds__(kTtmcWarps * 32) ttmc_bf16_kernel(const TtmcPa
           }
         }
       }
-      const uint4 *srcb = reinterpret_cast<const uint4 *>(UB + (size_t)ib * RB);
-      __nv_bfloat16 *brow = Bs + lane * SB;
+      constexpr int PB = RB / 8;
 #pragma unroll
-      for (int c = 0; c < RB / 8; ++c) *reinterpret_cast<uint4 *>(brow + 8 * c) = __ldg(srcb + c);
+      for (int it = lane; it < 32 * PB; it += 32) {
+        const int tt = it / PB, c = it % PB;
+        const uint32_t r = __shfl_sync(kFull, ib, tt);
+        *reinterpret_cast<uint4 *>(Bs + tt * SB + 8 * c) = __ldg(reinterpret_cast<const uint4 *>(UB + (size_t)r * RB) + c);
+      }
     }
     __syncwarp();
     uint32_t segs = starts | 1u;
