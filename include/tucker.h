@@ -208,6 +208,15 @@ TUCKER_API int tucker_phase_times(tucker_ctx *c, float *ms, int cap);
 /* Number of kernels libtucker has launched in this process, over all contexts. */
 TUCKER_API uint64_t tucker_kernel_launches(void);
 
+/*
+ * Self-test of the bounded device-side waits (no counterpart in the paper): one block
+ * polls a flag that nothing sets, with the bounded loop of the QRP grid barrier (at most
+ * max_polls polls about 100 ns apart), gives up and latches the timeout bit in the
+ * context's error word; the next tucker_sync_status returns TUCKER_ETIMEOUT and clears
+ * it.  The context stays usable.
+ */
+TUCKER_API tucker_status tucker_selftest_wait(tucker_ctx *c, uint64_t max_polls, void *stream);
+
 TUCKER_API const char *tucker_status_str(tucker_status s);
 /* Text of the last error recorded on this context ("" if none); valid until the next call. */
 TUCKER_API const char *tucker_last_error(const tucker_ctx *c);

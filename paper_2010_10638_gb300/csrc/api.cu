@@ -285,6 +285,11 @@ int tucker_phase_times(tucker_ctx *h, float *ms, int cap) {
 
 uint64_t tucker_kernel_launches(void) { return tk::g_launches.load(); }
 
+tucker_status tucker_selftest_wait(tucker_ctx *h, uint64_t max_polls, void *stream) {
+  if (!h) return TUCKER_EINVAL;
+  return tk::launch_wait_selftest(&h->c, (unsigned long long)max_polls, static_cast<cudaStream_t>(stream));
+}
+
 tucker_status tucker_init(tucker_ctx **out, int order, const int64_t *dims, int64_t nnz, const uint32_t *coords,
                           const float *vals, const int *ranks, const double *U0, uint64_t seed, uint32_t flags,
                           void *stream) {

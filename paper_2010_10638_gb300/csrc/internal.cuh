@@ -149,6 +149,7 @@ tucker_status qrp_run_f32(const float *A, int64_t m, int64_t n, int64_t lda, int
                           int64_t *piv, double *rdiag, QrpWork *w, int nb, cudaStream_t s);
 void gram_f32(const float *Y, int64_t m, int64_t n, double *S, cudaStream_t s);
 int qrp_blocks(int num_sms, int64_t m);
+tucker_status launch_wait_selftest(Ctx *c, unsigned long long max_polls, cudaStream_t s);
 
 // ---- K-d: core tensor and fit (core.cu)
 void launch_core(Ctx *c, const float *Y, const double *U, double *G, cudaStream_t s);

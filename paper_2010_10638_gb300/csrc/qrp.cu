@@ -1022,6 +1022,32 @@ static bool qrp_persistent(const AT *A, int64_t m, int64_t n, int64_t lda, int k
   return true;
 }
 
+// ============================================================================ wait self-test
+// One block polls a flag that nothing sets, with the bounded loop of the grid barrier
+// above, and latches kErrTimeout when it gives up.  It exercises the timeout path of the
+// library without any real wait going wrong.
+__global__ void wait_selftest_kernel(const unsigned *flag, unsigned long long max_polls, uint32_t *err) {
+  if (threadIdx.x != 0) return;
+  volatile const unsigned *f = flag;
+  unsigned long long polls = 0;
+  while (*f == 0u) {
+    if (++polls > max_polls) {
+      atomicOr(err, kErrTimeout);
+      return;
+    }
+    __nanosleep(100);
+  }
+}
+
+tucker_status launch_wait_selftest(Ctx *c, unsigned long long max_polls, cudaStream_t s) {
+  if (!c->qw.V) return TUCKER_ESTATE;
+  unsigned *flag = reinterpret_cast<unsigned *>(c->qw.V) + (c->qw.bytes / sizeof(unsigned)) - 1;  // last word
+  if (cudaMemsetAsync(flag, 0, sizeof(unsigned), s) != cudaSuccess) return TUCKER_ECUDA;
+  wait_selftest_kernel<<<1, 32, 0, s>>>(flag, max_polls, c->d_err);
+  ::tk::count_launch();
+  return cudaGetLastError() == cudaSuccess ? TUCKER_OK : TUCKER_ECUDA;
+}
+
 // ---------------------------------------------------------------------------- host side
 int qrp_blocks(int num_sms, int64_t m) {
   int64_t b = std::max<int64_t>(1, std::min<int64_t>((int64_t)num_sms, (m + 31) / 32));

@@ -36,7 +36,8 @@ STATUS = {0: "TUCKER_OK", 1: "TUCKER_EINVAL", 2: "TUCKER_ERANK", 3: "TUCKER_ENOM
 EXPORTS = ["tucker_init", "ttmc_mode", "qrp_leading", "qrp_leading_work_bytes", "hooi_iter", "core_tensor",
            "tucker_get_factor", "tucker_set_factor", "tucker_loss_grad", "tucker_nnz", "tucker_norm2",
            "tucker_sync_status", "tucker_free", "tucker_status_str", "tucker_last_error", "tucker_set_profiling",
-           "tucker_phase_times", "tucker_kernel_launches", "qrp_leading_noalloc", "qrp_leading_noalloc_max_bytes"]
+           "tucker_phase_times", "tucker_kernel_launches", "qrp_leading_noalloc", "qrp_leading_noalloc_max_bytes",
+           "tucker_selftest_wait"]
 
 
 class TuckerError(RuntimeError):
@@ -89,6 +90,8 @@ def load(path: str = LIB_PATH):
     lib.qrp_leading_noalloc.restype = cint
     lib.qrp_leading_noalloc_max_bytes.argtypes = []
     lib.qrp_leading_noalloc_max_bytes.restype = csz
+    lib.tucker_selftest_wait.argtypes = [vp, u64, vp]
+    lib.tucker_selftest_wait.restype = cint
     lib.tucker_kernel_launches.argtypes = []
     lib.tucker_kernel_launches.restype = ctypes.c_uint64
     for name in ("tucker_init", "ttmc_mode", "qrp_leading", "hooi_iter", "core_tensor", "tucker_get_factor",
@@ -335,3 +338,7 @@ def qrp_leading_noalloc(A: torch.Tensor, k: int, stream=None):
     _check(load().qrp_leading_noalloc(A.data_ptr(), m, n, n, int(k), Q.data_ptr(), piv.data_ptr(), rdiag.data_ptr(),
                                       _stream(stream)), "qrp_leading_noalloc")
     return Q, piv, rdiag
+
+
+def tucker_selftest_wait(ctx: Context, max_polls: int, stream=None) -> None:
+    _check(load().tucker_selftest_wait(ctx.handle, int(max_polls), _stream(stream)), "tucker_selftest_wait", ctx)

@@ -177,3 +177,20 @@ def test_allocation_failure_is_reported_and_recoverable(monkeypatch):
     monkeypatch.delenv("TUCKER_FAIL_ALLOC_AT")
     ctx = T.tucker_init(dims, w.coords, w.vals, ranks, w.U0)
     assert T.tucker_nnz(ctx) == w.workload.nnz
+
+
+def test_bounded_wait_times_out_and_context_survives():
+    """A device wait that can never finish gives up after its poll limit, the timeout is
+    reported by the next synchronising call, and the context keeps working."""
+    T = lib()
+    w = synth.make("tiny-100^3")
+    ctx = T.tucker_init(w.workload.dims, w.coords, w.vals, w.workload.ranks, w.U0)
+    T.tucker_sync_status(ctx)  # clean
+    T.tucker_selftest_wait(ctx, 20_000)
+    with pytest.raises(T.TuckerError) as e:
+        T.tucker_sync_status(ctx)
+    assert e.value.name == "TUCKER_ETIMEOUT"
+    T.tucker_sync_status(ctx)  # cleared
+    Y = T.ttmc_mode(ctx, 0)
+    assert torch.isfinite(Y).all()
+    assert 0.0 < T.hooi_iter(ctx) < 1.0
