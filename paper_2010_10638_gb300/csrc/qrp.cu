@@ -385,6 +385,7 @@ struct PArgs {
   int64_t m, n, lda;
   int k;
   double *V, *F, *part, *vn, *vref, *T, *Q;
+  double *scal;  // [0]: y_jj of the current step, written by the block owning row j
   int64_t ldq;
   int *flag, *nflag;
   unsigned *bar;   // [0] arrivals, [1] generation, [2] abort flag (cleared per call)
@@ -699,7 +700,7 @@ __global__ void __launch_bounds__(kPThreads) qrp_persistent_kernel(PArgs a) {
   __shared__ double s_u[64];
   __shared__ double s_f[64];
   __shared__ double s_vj[64];
-  __shared__ double s_v0, s_tau;
+  __shared__ double s_v0, s_tau, s_dv;
   __shared__ int s_nflag;
   const int64_t n = a.n, m = a.m;
   const int k = a.k;
@@ -723,6 +724,8 @@ __global__ void __launch_bounds__(kPThreads) qrp_persistent_kernel(PArgs a) {
     colsum_rows<AT, true>(a, r0, r1, [](int64_t) { return 0.0; }, red, stage);
   for (int64_t c = threadIdx.x; c < n; c += kPThreads) perm_s[c] = (int)c;
   for (int q = threadIdx.x; q < k * k; q += kPThreads) Ts[q] = 0.0;
+  if (b == 0)  // per-step counts of recomputed norms; stepped into only after later barriers
+    for (int q = threadIdx.x; q < k; q += kPThreads) a.nflag[q] = 0;
   if (!grid_sync(a)) return timeout_exit(a);
   for (int64_t c = gw; c < n; c += nw) {
     const double t = warp_part_sum(a, c);
@@ -769,6 +772,7 @@ __global__ void __launch_bounds__(kPThreads) qrp_persistent_kernel(PArgs a) {
       y = (i >= j) ? y : 0.0;
       s2 = fma(y, y, s2);
       a.V[i * k + j] = y;
+      if (i == j) a.scal[0] = y;  // x0 of the reflector, read by every block after the barrier
       if (i > j) {  // second pass over the (L1-resident) row: V[i, l] y_i for l < 16
         if ((k & 1) == 0) {
           const double2 *v2 = reinterpret_cast<const double2 *>(vrow);
@@ -822,10 +826,21 @@ __global__ void __launch_bounds__(kPThreads) qrp_persistent_kernel(PArgs a) {
         }
       }
     }
+    // ---- A^T y over this block's rows >= j (no barrier: v_j differs from y only in row j,
+    //      whose term is added after the barrier as (v_jj - y_jj) A[j, :])
+    {
+      __syncthreads();  // this block's y rows (written above) are read back by the staging
+      const int64_t rb0 = max(r0, (int64_t)j);
+      auto yfun = [&](int64_t i) { return __ldcg(a.V + i * k + j); };
+      if (vec4)
+        colsum_rows_f32x4<false>(a, rb0, max(rb0, r1), yfun, red4, static_cast<float2 *>(stage));
+      else
+        colsum_rows<AT, false>(a, rb0, max(rb0, r1), yfun, red, stage);
+    }
     if (!grid_sync(a)) return timeout_exit(a);
     // ---- reflector scalars, identically in every block (one warp)
     if (warp == 0) {
-      const double x0 = __ldcg(a.V + (int64_t)j * k + j);
+      const double x0 = __ldcg(a.scal);
       double t = 0.0;
 #pragma unroll 4
       for (int bb = lane; bb < nb; bb += 32) t += __ldcg(a.part + (int64_t)bb * ld + n + k);
@@ -842,23 +857,15 @@ __global__ void __launch_bounds__(kPThreads) qrp_persistent_kernel(PArgs a) {
         }
         s_v0 = v0;
         s_tau = tau;
+        s_dv = v0 - x0;
         if (b == 0) {
           if (a.rdiag) a.rdiag[j] = beta;
           if (a.piv) a.piv[j] = c0;
-          a.nflag[j] = 0;
         }
       }
     }
     __syncthreads();
-    const double v0 = s_v0, tau = s_tau;
-    // ---- B: A^T v_j over this block's rows (v_j is zero above row j)
-    const int64_t rb0 = max(r0, (int64_t)j);
-    auto vfun = [&](int64_t i) { return (i == j) ? v0 : __ldcg(a.V + i * k + j); };
-    if (vec4)
-      colsum_rows_f32x4<false>(a, rb0, max(rb0, r1), vfun, red4, static_cast<float2 *>(stage));
-    else
-      colsum_rows<AT, false>(a, rb0, max(rb0, r1), vfun, red, stage);
-    if (!grid_sync(a)) return timeout_exit(a);
+    const double v0 = s_v0, tau = s_tau, dv = s_dv;
     // ---- C: u = V^T v_j, this block's T, then F[:, j], row j of R, norm downdate
     // Row j of V gets v_jj only now: every block read x0 from it between the first two
     // barriers of this step, and until then only its owner used v_jj (from s_v0).
@@ -890,7 +897,7 @@ __global__ void __launch_bounds__(kPThreads) qrp_persistent_kernel(PArgs a) {
       const double f1 = (lane + 32 < j) ? __ldcg(frow + lane + 32) : 0.0;
       const double ajc = aval<AT>(a, j, c);
       const double vnc = __ldcg(a.vn + c), ref = __ldcg(a.vref + c);
-      const double w = warp_part_sum(a, c);
+      const double w = fma(dv, ajc, warp_part_sum(a, c));  // A^T v = A^T y + (v_jj - y_jj) A[j, :]
       double corr = 0.0, rv = 0.0;
       if (lane < j) {
         corr = f0 * s_u[lane];
@@ -1007,6 +1014,7 @@ static bool qrp_persistent(const AT *A, int64_t m, int64_t n, int64_t lda, int k
   a.vref = w->vref;
   a.T = w->T;
   a.Q = Q;
+  a.scal = w->scal;
   a.ldq = ldq;
   a.flag = w->flag;
   a.nflag = w->nflag;
