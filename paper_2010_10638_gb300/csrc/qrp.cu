@@ -361,10 +361,11 @@ __global__ void qrp_q_kernel(QrpArgs a, double *Q, int64_t ldq) {
 // ============================================================================ persistent form
 // One cooperative launch runs all k steps.  Blocks own a contiguous range of rows for
 // the row-parallel phases and a strided set of column positions for the column
-// phases; three grid barriers separate the phases of a step:
-//   A  rows of the updated pivot column -> V[:, j], partial ||.||^2   | barrier
-//      every block forms tau, beta, v_jj from the same partials (identical values)
-//   B  partial A^T v_j (all columns) and V^T v_j                      | barrier
+// phases; two grid barriers separate the phases of a step:
+//   A  rows of the updated pivot column y -> V[:, j], partial ||y||^2, then, on the
+//      same rows, partial A^T y (all columns) and V^T y                 | barrier
+//      every block forms tau, beta, v_jj from the same partials (identical values);
+//      v_j differs from y only in row j, so A^T v_j = A^T y + (v_jj - y_jj) A[j, :]
 //   C  per column: F[c, j], R[j, c], norm downdate (warp per column)   | barrier
 //      [rare: exact recomputation of cancelled norms, two more barriers]
 //      every block picks the next pivot from the same norms and swaps it in its own
