@@ -50,6 +50,7 @@ struct QrpWork {
   double *V = nullptr;       // m x k reflectors, V[i*k + j]
   double *F = nullptr;       // n x k, F[c*k + j]
   double *part = nullptr;    // nb x (n + k) block partial sums
+  size_t part_elems = 0;     // doubles in `part`
   double *vn = nullptr;      // n trailing squared norms (current column order)
   double *vref = nullptr;    // n squared norms at their last exact computation
   int *perm = nullptr;       // n current column order (original indices)
@@ -143,6 +144,11 @@ size_t qrp_work_bytes(int64_t m, int64_t n, int k, int nb);
 void qrp_bind_work(QrpWork *w, void *base, int64_t m, int64_t n, int k, int nb);
 // A is m x n (row stride lda) of type float or double; writes Q (m x k, row stride ldq),
 // piv (int64, may be null), rdiag (may be null).
+// Cluster form of the QRP (qrp_cluster.cu): false when its shared-memory plan does not
+// fit (the caller runs another form); *err reports a launch that was attempted and failed.
+template <typename AT>
+bool qrp_cluster(const AT *A, int64_t m, int64_t n, int64_t lda, int k, double *Q, int64_t ldq, int64_t *piv,
+                 double *rdiag, QrpWork *w, cudaStream_t s, cudaError_t *err);
 tucker_status qrp_run_f64(const double *A, int64_t m, int64_t n, int64_t lda, int k, double *Q, int64_t ldq,
                           int64_t *piv, double *rdiag, QrpWork *w, int nb, cudaStream_t s);
 tucker_status qrp_run_f32(const float *A, int64_t m, int64_t n, int64_t lda, int k, double *Q, int64_t ldq,

@@ -25,6 +25,7 @@
 #include <algorithm>
 #include <cfloat>
 
+#include "dfloat.cuh"
 #include "internal.cuh"
 
 namespace tk {
@@ -434,21 +435,6 @@ __device__ __forceinline__ void timeout_exit(const PArgs &a) {
       for (int j = 0; j < a.k; ++j) a.rdiag[j] = qnan;
     a.Q[0] = qnan;  // a factor with a NaN makes the failure visible downstream
   }
-}
-
-// double-float accumulation of exact FP32 products: s += a * (bh + bl)
-struct DF {
-  float hi = 0.f, lo = 0.f;
-};
-__device__ __forceinline__ void df_fma(DF &s, float a, float bh, float bl) {
-  const float p = a * bh;
-  const float e = fmaf(a, bh, -p);
-  const float q = a * bl;
-  const float t = s.hi + p;
-  const float bp = t - s.hi;
-  const float err = (s.hi - (t - bp)) + (p - bp);
-  s.hi = t;
-  s.lo += err + (e + q);
 }
 
 __device__ __forceinline__ double block_sum_p(double v, double *red) {
@@ -1102,6 +1088,7 @@ void qrp_bind_work(QrpWork *w, void *base, int64_t m, int64_t n, int k, int nb) 
   w->V = (double *)take(sizeof(double) * (size_t)std::max<int64_t>(m * k, 1));
   w->F = (double *)take(sizeof(double) * (size_t)std::max<int64_t>(n * k, 1));
   w->part = (double *)take(sizeof(double) * (size_t)(part_rows * part_ld));
+  w->part_elems = (size_t)(part_rows * part_ld);
   w->vn = (double *)take(sizeof(double) * (size_t)std::max<int64_t>(n, 1));
   w->vref = (double *)take(sizeof(double) * (size_t)std::max<int64_t>(n, 1));
   w->perm = (int *)take(sizeof(int) * (size_t)std::max<int64_t>(n, 1));
@@ -1124,6 +1111,9 @@ static tucker_status qrp_run(const AT *A, int64_t m, int64_t n, int64_t lda, int
   if (k > 64) return TUCKER_ERANK;  // F rows are staged in 64-wide shared buffers
   {
     cudaError_t e = cudaSuccess;
+    if (qrp_cluster<AT>(A, m, n, lda, k, Q, ldq, piv, rdiag, w, s, &e))
+      return e == cudaSuccess ? TUCKER_OK : TUCKER_ECUDA;
+    if (e != cudaSuccess) return TUCKER_ECUDA;
     if (qrp_persistent<AT>(A, m, n, lda, k, Q, ldq, piv, rdiag, w, nb, s, &e))
       return e == cudaSuccess ? TUCKER_OK : TUCKER_ECUDA;
   }

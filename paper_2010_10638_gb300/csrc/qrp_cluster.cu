@@ -1,0 +1,921 @@
+// K-c, cluster form: the Householder QR with column pivoting of qrp.cu (Section III-D;
+// same implicit update A P - V F^T, same reflector, norm-downdate and pivot rules) run
+// with one grid-wide synchronisation per reflector.
+//
+// Rows of A are split over all blocks of one launch; columns are split over the S
+// blocks of each thread-block cluster (block `rank` owns the columns c = rank mod S),
+// and every cluster repeats the same column work.  Each block keeps in shared memory
+// its rows of V, the F rows, norms and flags of its columns, the column order, T, the
+// top k x k corner of V, and as many of its rows of A as fit.  A step j is
+//   rows     y = A[:, p] - V F[p, :]^T on this block's rows (F[p, :] read from the
+//            owning block's shared memory); partial sums of A^T y, V^T y, ||y||^2,
+//            and from the block owning row j, y_jj and V[j, :j]
+//   reduce   the partial vectors of a cluster are added through distributed shared
+//            memory; with several clusters one slice per block goes to global memory,
+//            the clusters meet at one bounded counter barrier, and every block adds
+//            the cluster sums it needs (its columns and the scalars) in cluster order
+//   columns  the reflector (tau, beta, v_jj), F[:, j], row j of R and the norm
+//            downdates of this block's columns
+//   pivot    each block proposes the largest remaining norm of its columns; after one
+//            cluster barrier every block takes the best proposal (lowest position on
+//            ties), so all copies of the column order stay identical.
+// A^T v_j is A^T y + (v_jj - y_jj) A[j, :] (v_j differs from y only in row j), so the
+// pass over A starts before the reflector is known.  FP32 A: exact products summed in
+// double-float pairs (dfloat.cuh) and converted to FP64 once per column; FP64 A: FMA.
+// The FP64 pipe is narrow on this GPU, so FP64 work is kept to what the method needs
+// and is not issued for idle lanes in long loops.  Downdated norms that lose more than
+// sqrt(eps) of their last exact value are recomputed exactly (rare).
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <cfloat>
+#include <climits>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+
+#include "dfloat.cuh"
+#include "internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace tk {
+namespace {
+
+constexpr int kCT = 512;  // threads per block, one block per SM
+constexpr int kCW = kCT / 32;
+constexpr unsigned long long kCSpin = 1ull << 25;  // polls before a barrier wait gives up
+
+struct CArgs {
+  const void *A;
+  int64_t m, n, lda;
+  int k;
+  int L;          // partial-vector length n + 2k + 2
+  int nclusters;  // clusters in the launch
+  int vec4;       // FP32 A read as float4 (n % 4 == 0, lda % 4 == 0, 16-byte aligned)
+  int64_t rows_per;     // rows of A per block
+  int64_t rows_cached;  // leading rows of each block's range kept in shared memory
+  double *slots;        // [2][nclusters][L] cluster sums (alternating buffers)
+  unsigned *bar;        // [0] arrival count, [2] abort flag
+  uint32_t *err;        // where a timed-out wait is reported
+  double *Q;
+  int64_t ldq;
+  int64_t *piv;
+  double *rdiag;
+};
+
+// Dynamic shared memory of one block; the same arithmetic on host and device.
+struct CLayout {
+  size_t Fo, vno, vrefo, ajo, svo, svs, flago, doneo, red, Ts, Vt, Ms, su, Vs, red4, ys, perm, posof, cand, As, total;
+  int kp;      // row stride of Vs in doubles (odd: rows fall in different banks)
+  int64_t no;  // columns per block, rounded up
+};
+
+__host__ __device__ inline size_t c16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+__host__ __device__ inline CLayout clayout(int64_t n, int k, int L, int S, int64_t rows_per, int64_t rows_cached,
+                                           int esize) {
+  CLayout l{};
+  l.kp = k | 1;
+  l.no = (n + S - 1) / S;
+  const size_t no = (size_t)l.no;
+  size_t o = 0;
+  l.Fo = o;    o += c16(sizeof(double) * (size_t)k * no);  // F of this block's columns: Fo[l * no + lc]
+  l.vno = o;   o += c16(sizeof(double) * no);
+  l.vrefo = o; o += c16(sizeof(double) * no);
+  l.ajo = o;   o += c16(sizeof(double) * no);              // A[j, c] of this block's columns
+  l.svo = o;   o += c16(sizeof(double) * no);              // reduced A^T y of this block's columns
+  l.svs = o;   o += c16(sizeof(double) * (size_t)(2 * k + 2));  // reduced scalars
+  l.flago = o; o += c16(sizeof(int) * no);
+  l.doneo = o; o += c16(sizeof(int) * no);
+  l.red = o;   o += c16(sizeof(double) * 2 * (size_t)L);  // this block's partials, two buffers
+  l.Ts = o;    o += c16(sizeof(double) * (size_t)k * k);
+  l.Vt = o;    o += c16(sizeof(double) * (size_t)k * k);  // V[0:k, 0:k]
+  l.Ms = o;    o += c16(sizeof(double) * (size_t)k * k);
+  l.su = o;    o += c16(sizeof(double) * 64);
+  l.Vs = o;    o += c16(sizeof(double) * (size_t)rows_per * l.kp);  // this block's rows of V
+  l.red4 = o;  o += c16(sizeof(double) * 2 * kCT);        // reduction scratch (8 KB)
+  l.ys = o;    o += c16(sizeof(double) * (size_t)rows_per);  // y per row (float2 or double)
+  l.perm = o;  o += c16(sizeof(int) * (size_t)n);
+  l.posof = o; o += c16(sizeof(int) * (size_t)n);
+  l.cand = o;  o += 32;                                    // pivot proposal: key, position, any flag
+  l.As = o;    o += c16((size_t)esize * (size_t)rows_cached * (size_t)n);
+  l.total = o;
+  return l;
+}
+
+// global -> shared copies without a register round trip (completed by cp.async.wait_all)
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T *dst, const T *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (sizeof(T) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+// double-float addition a += b (TwoSum of the high parts, then renormalisation)
+__device__ __forceinline__ void df_add(DF &a, const DF b) {
+  const float s = a.hi + b.hi;
+  const float bp = s - a.hi;
+  float e = (a.hi - (s - bp)) + (b.hi - bp);
+  e += a.lo + b.lo;
+  a.hi = s + e;
+  a.lo = e - (a.hi - s);
+}
+
+// Ordering key of a squared norm (>= 0): its bit pattern without the sign (so -0 = 0);
+// NaN gets -1 and is never preferred.  Integer compares keep argmax off the FP64 pipe.
+__device__ __forceinline__ long long norm_key(double v) {
+  const long long b = __double_as_longlong(v) & 0x7fffffffffffffffll;
+  return b > 0x7ff0000000000000ll ? -1ll : b;
+}
+
+// Bounded counter barrier of the clusters' leading threads: every arrival adds one
+// (release); a leader waits until the count reaches target = calls so far x clusters.
+__device__ bool leaders_barrier(const CArgs &a, unsigned target) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], 1;\n" ::"l"(a.bar) : "memory");
+  unsigned long long spins = 0;
+  while (true) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(a.bar) : "memory");
+    if (v >= target) break;
+    if (++spins > kCSpin) {
+      atomicOr(a.bar + 2, 1u);
+      atomicOr(a.err, kErrTimeout);
+      break;
+    }
+    if ((spins & 255u) == 0u && *(volatile unsigned *)(a.bar + 2)) break;  // another cluster gave up
+    __nanosleep(20);
+  }
+  return *(volatile unsigned *)(a.bar + 2) == 0u;
+}
+
+// sum over the S blocks of the cluster of entry q of their vectors `mine` (shared
+// memory), in rank order; all S loads are issued before the additions
+__device__ __forceinline__ double peer_sum(cg::cluster_group &cl, double *mine, unsigned S, int q) {
+  double x[16];
+#pragma unroll
+  for (unsigned r = 0; r < 16; ++r) x[r] = (r < S) ? cl.map_shared_rank(mine, r)[q] : 0.0;
+  double t = x[0];
+#pragma unroll
+  for (unsigned r = 1; r < 16; ++r)
+    if (r < S) t += x[r];
+  return t;
+}
+
+struct Team {
+  unsigned S, rank;
+  int nown;        // columns owned by this block
+  unsigned epoch;  // grid-wide reductions so far
+};
+
+// Sums of the blocks' partial vectors `mine` (L doubles each, shared memory), in the
+// same order in every block: entries of this block's columns into svo, the scalar
+// entries n .. L-1 into svs.  False when a wait timed out (then no block reads a
+// peer's memory any more).
+__device__ bool allreduce(const CArgs &a, cg::cluster_group &cl, Team &tm, double *mine, double *svo, double *svs,
+                          int par, int *s_ok) {
+  const int L = a.L, n = (int)a.n, ns = 2 * a.k + 2, need = tm.nown + ns;
+  auto entry = [&](int t) { return t < tm.nown ? (int)tm.rank + (int)tm.S * t : n + (t - tm.nown); };
+  auto store = [&](int t, double v) {
+    if (t < tm.nown)
+      svo[t] = v;
+    else
+      svs[t - tm.nown] = v;
+  };
+  cl.sync();  // every block of the cluster has written its partials
+  if (a.nclusters == 1) {
+    for (int t = threadIdx.x; t < need; t += kCT) store(t, peer_sum(cl, mine, tm.S, entry(t)));
+    __syncthreads();
+    return true;  // `mine` alternates between two buffers: the next write cannot race these reads
+  }
+  const int cid = (int)(blockIdx.x / tm.S);
+  double *slot = a.slots + ((size_t)par * a.nclusters + cid) * L;
+  const int per = (int)((L + tm.S - 1) / tm.S);
+  const int q0 = (int)tm.rank * per, q1 = min(L, q0 + per);
+  bool wrote = false;
+  for (int q = q0 + threadIdx.x; q < q1; q += kCT) {
+    slot[q] = peer_sum(cl, mine, tm.S, q);
+    wrote = true;
+  }
+  if (wrote) __threadfence();
+  cl.sync();  // the cluster's sum is stored
+  tm.epoch += 1;
+  if (tm.rank == 0 && threadIdx.x == 0) *s_ok = leaders_barrier(a, tm.epoch * (unsigned)a.nclusters) ? 1 : 0;
+  cl.sync();  // the leader passed the barrier (or gave up)
+  const int ok = *cl.map_shared_rank(s_ok, 0);
+  if (!ok) {
+    cl.sync();  // nobody reads rank 0's flag once it may have left
+    return false;
+  }
+  const double *base = a.slots + (size_t)par * a.nclusters * L;
+  for (int t = threadIdx.x; t < need; t += kCT) {
+    const int q = entry(t);
+    double sum = 0.0;
+    for (int c0 = 0; c0 < a.nclusters; c0 += 16) {  // 16 loads in flight, added in cluster order
+      double x[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) x[u] = (c0 + u < a.nclusters) ? __ldcg(base + (size_t)(c0 + u) * L + q) : 0.0;
+#pragma unroll
+      for (int u = 0; u < 16; ++u)
+        if (c0 + u < a.nclusters) sum += x[u];
+    }
+    store(t, sum);
+  }
+  __syncthreads();
+  return true;
+}
+
+// Rows [s0, s1) (local indices) of four adjacent columns into double-float sums.
+template <bool GLOBAL, bool SQUARE>
+__device__ __forceinline__ void seg4(const float4 *base, int64_t stride4, int64_t s0, int64_t s1, int rl, int nrl,
+                                     const float2 *y2, DF &d0, DF &d1, DF &d2, DF &d3) {
+  int64_t ii = s0 + rl;
+  for (; ii + 7 * nrl < s1; ii += 8 * nrl) {
+    float4 x[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const float4 *p = base + (ii + u * nrl) * stride4;
+      x[u] = GLOBAL ? __ldg(p) : *p;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (SQUARE) {
+        df_fma(d0, x[u].x, x[u].x, 0.f);
+        df_fma(d1, x[u].y, x[u].y, 0.f);
+        df_fma(d2, x[u].z, x[u].z, 0.f);
+        df_fma(d3, x[u].w, x[u].w, 0.f);
+      } else {
+        const float2 vv = y2[ii + u * nrl];
+        df_fma(d0, x[u].x, vv.x, vv.y);
+        df_fma(d1, x[u].y, vv.x, vv.y);
+        df_fma(d2, x[u].z, vv.x, vv.y);
+        df_fma(d3, x[u].w, vv.x, vv.y);
+      }
+    }
+  }
+  for (; ii < s1; ii += nrl) {
+    const float4 *p = base + ii * stride4;
+    const float4 x = GLOBAL ? __ldg(p) : *p;
+    if (SQUARE) {
+      df_fma(d0, x.x, x.x, 0.f);
+      df_fma(d1, x.y, x.y, 0.f);
+      df_fma(d2, x.z, x.z, 0.f);
+      df_fma(d3, x.w, x.w, 0.f);
+    } else {
+      const float2 vv = y2[ii];
+      df_fma(d0, x.x, vv.x, vv.y);
+      df_fma(d1, x.y, vv.x, vv.y);
+      df_fma(d2, x.z, vv.x, vv.y);
+      df_fma(d3, x.w, vv.x, vv.y);
+    }
+  }
+}
+
+__device__ __forceinline__ DF df_of(float2 p) {
+  DF d;
+  d.hi = p.x;
+  d.lo = p.y;
+  return d;
+}
+
+// out[c], c < n: sum over local rows li in [l0, nrows) of A[r0 + li, c] * y_li (SQUARE:
+// A[r0 + li, c]^2).  Rows li < ncache come from the shared copy As (row stride n).
+// `scratch` holds 2 * kCT doubles.
+template <typename AT, bool SQUARE>
+__device__ void ccolsum(const CArgs &a, const AT *As, int64_t ncache, int64_t r0, int64_t l0, int64_t nrows,
+                        const void *ys, void *scratch, double *out) {
+  const int64_t n = a.n;
+  const AT *A = static_cast<const AT *>(a.A);
+  l0 = min(l0, nrows);
+  if constexpr (sizeof(AT) == 4) {
+    float2 *red = static_cast<float2 *>(scratch);  // 2 x kCT double-float pairs
+    const float2 *y2 = static_cast<const float2 *>(ys);
+    if (a.vec4) {
+      const int64_t nq = n / 4, ld4 = a.lda / 4, sn4 = n / 4;
+      int cw = 8;
+      while (cw < nq && cw < kCT) cw <<= 1;
+      const int nrl = kCT / cw, cq = threadIdx.x % cw, rl = threadIdx.x / cw;
+      for (int64_t q0 = 0; q0 < nq; q0 += cw) {
+        const int64_t qc = q0 + cq;
+        DF d[4];
+        if (qc < nq) {
+          seg4<false, SQUARE>(reinterpret_cast<const float4 *>(As) + qc, sn4, l0, min(nrows, ncache), rl, nrl, y2,
+                              d[0], d[1], d[2], d[3]);
+          seg4<true, SQUARE>(reinterpret_cast<const float4 *>(A) + r0 * ld4 + qc, ld4, max(l0, ncache), nrows, rl,
+                             nrl, y2, d[0], d[1], d[2], d[3]);
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {  // two columns of the four at a time through the scratch
+          __syncthreads();
+          red[threadIdx.x] = make_float2(d[2 * h].hi, d[2 * h].lo);
+          red[kCT + threadIdx.x] = make_float2(d[2 * h + 1].hi, d[2 * h + 1].lo);
+          __syncthreads();
+          if (rl == 0 && qc < nq) {
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+              DF t = d[2 * h + q];
+              for (int r = 1; r < nrl; ++r) df_add(t, df_of(red[q * kCT + r * cw + cq]));
+              out[4 * qc + 2 * h + q] = (double)t.hi + (double)t.lo;
+            }
+          }
+        }
+      }
+      __syncthreads();
+      return;
+    }
+    int cw = 32;
+    while (cw < n && cw < kCT) cw <<= 1;
+    const int nrl = kCT / cw, cl = threadIdx.x % cw, rl = threadIdx.x / cw;
+    for (int64_t c0 = 0; c0 < n; c0 += cw) {
+      const int64_t c = c0 + cl;
+      DF d;
+      if (c < n) {
+        for (int64_t li = l0 + rl; li < nrows; li += nrl) {
+          const float x = li < ncache ? (float)As[li * n + c] : (float)__ldg(A + (r0 + li) * a.lda + c);
+          if (SQUARE) {
+            df_fma(d, x, x, 0.f);
+          } else {
+            const float2 vv = y2[li];
+            df_fma(d, x, vv.x, vv.y);
+          }
+        }
+      }
+      __syncthreads();
+      red[threadIdx.x] = make_float2(d.hi, d.lo);
+      __syncthreads();
+      if (rl == 0 && c < n) {
+        DF t = d;
+        for (int r = 1; r < nrl; ++r) df_add(t, df_of(red[r * cw + cl]));
+        out[c] = (double)t.hi + (double)t.lo;
+      }
+    }
+    __syncthreads();
+  } else {
+    double *red = static_cast<double *>(scratch);
+    const double *yd = static_cast<const double *>(ys);
+    int cw = 32;
+    while (cw < n && cw < kCT) cw <<= 1;
+    const int nrl = kCT / cw, cl = threadIdx.x % cw, rl = threadIdx.x / cw;
+    for (int64_t c0 = 0; c0 < n; c0 += cw) {
+      const int64_t c = c0 + cl;
+      double acc = 0.0;
+      if (c < n) {
+        for (int64_t li = l0 + rl; li < nrows; li += nrl) {
+          const double x = li < ncache ? (double)As[li * n + c] : (double)__ldg(A + (r0 + li) * a.lda + c);
+          acc = fma(x, SQUARE ? x : yd[li], acc);
+        }
+      }
+      __syncthreads();
+      red[threadIdx.x] = acc;
+      __syncthreads();
+      if (rl == 0 && c < n) {
+        double t = acc;
+        for (int r = 1; r < nrl; ++r) t += red[r * cw + cl];
+        out[c] = t;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// The pivot for position j0: every block proposes its largest remaining norm (lowest
+// position on ties), one cluster barrier, then every block takes the best proposal and
+// swaps it into position j0.  When some block holds a norm flagged for exact
+// recomputation nothing is swapped and true is returned (the same answer in every
+// block).  The cluster barrier also publishes this step's F rows to the peers.
+__device__ bool choose_pivot(cg::cluster_group &cl, const Team &tm, int j0, int64_t n, const double *vno,
+                             const int *flago, int *doneo, int *perm, int *posof, unsigned long long *cand,
+                             int *s_res) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp == 0) {
+    long long best = -1;
+    int bp = INT_MAX, anyf = 0;
+    for (int lc = lane; lc < tm.nown; lc += 32) {
+      anyf |= flago[lc];
+      if (doneo[lc]) continue;
+      const long long key = norm_key(vno[lc]);
+      const int p = posof[tm.rank + tm.S * lc];
+      if (key > best || (key == best && key >= 0 && p < bp)) {
+        best = key;
+        bp = p;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const long long k2 = __shfl_xor_sync(0xffffffffu, best, o);
+      const int p2 = __shfl_xor_sync(0xffffffffu, bp, o);
+      if (k2 > best || (k2 == best && p2 < bp)) {
+        best = k2;
+        bp = p2;
+      }
+      anyf |= __shfl_xor_sync(0xffffffffu, anyf, o);
+    }
+    if (lane == 0) {
+      cand[0] = (unsigned long long)best;
+      cand[1] = (unsigned long long)(unsigned)bp;
+      cand[2] = (unsigned long long)anyf;
+    }
+  }
+  cl.sync();
+  if (warp == 0) {
+    long long best = -1;
+    int bp = INT_MAX, anyf = 0;
+    if (lane < (int)tm.S) {
+      const unsigned long long *pc = cl.map_shared_rank(cand, (unsigned)lane);
+      best = (long long)pc[0];
+      bp = (int)(unsigned)pc[1];
+      anyf = (int)pc[2];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const long long k2 = __shfl_xor_sync(0xffffffffu, best, o);
+      const int p2 = __shfl_xor_sync(0xffffffffu, bp, o);
+      if (k2 > best || (k2 == best && p2 < bp)) {
+        best = k2;
+        bp = p2;
+      }
+      anyf |= __shfl_xor_sync(0xffffffffu, anyf, o);
+    }
+    if (lane == 0) {
+      if (!anyf && bp != INT_MAX && bp < n) {
+        const int cj = perm[j0], cb = perm[bp];
+        perm[j0] = cb;
+        perm[bp] = cj;
+        posof[cb] = j0;
+        posof[cj] = bp;
+        if (cb % (int)tm.S == (int)tm.rank) doneo[cb / (int)tm.S] = 1;
+      }
+      *s_res = anyf;
+    }
+  }
+  __syncthreads();
+  return *s_res != 0;
+}
+
+__device__ void cbail(const CArgs &a) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+    if (a.rdiag)
+      for (int j = 0; j < a.k; ++j) a.rdiag[j] = qnan;
+    a.Q[0] = qnan;  // a factor with a NaN makes the failure visible downstream
+  }
+}
+
+template <typename AT>
+__global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ double s_f[64];  // F[p, 0:j] of the current pivot column
+  __shared__ double s_sc[4];  // v_jj, tau, v_jj - y_jj
+  __shared__ int s_ok, s_res;
+  cg::cluster_group cl = cg::this_cluster();
+  Team tm;
+  tm.S = cl.num_blocks();
+  tm.rank = cl.block_rank();
+  tm.epoch = 0;
+  const int64_t n = a.n, m = a.m;
+  const int k = a.k, L = a.L;
+  const CLayout lay = clayout(n, k, L, (int)tm.S, a.rows_per, a.rows_cached, (int)sizeof(AT));
+  tm.nown = (int)((n - (int64_t)tm.rank + tm.S - 1) / tm.S);
+  const int64_t no = lay.no;
+  double *Fo = reinterpret_cast<double *>(sm + lay.Fo);
+  double *vno = reinterpret_cast<double *>(sm + lay.vno);
+  double *vrefo = reinterpret_cast<double *>(sm + lay.vrefo);
+  double *ajo = reinterpret_cast<double *>(sm + lay.ajo);
+  double *svo = reinterpret_cast<double *>(sm + lay.svo);
+  double *svs = reinterpret_cast<double *>(sm + lay.svs);
+  int *flago = reinterpret_cast<int *>(sm + lay.flago);
+  int *doneo = reinterpret_cast<int *>(sm + lay.doneo);
+  double *red = reinterpret_cast<double *>(sm + lay.red);
+  double *Ts = reinterpret_cast<double *>(sm + lay.Ts);
+  double *Vt = reinterpret_cast<double *>(sm + lay.Vt);
+  double *Ms = reinterpret_cast<double *>(sm + lay.Ms);
+  double *su = reinterpret_cast<double *>(sm + lay.su);
+  double *Vs = reinterpret_cast<double *>(sm + lay.Vs);
+  double *red4 = reinterpret_cast<double *>(sm + lay.red4);
+  void *ys = sm + lay.ys;
+  int *perm = reinterpret_cast<int *>(sm + lay.perm);
+  int *posof = reinterpret_cast<int *>(sm + lay.posof);
+  unsigned long long *cand = reinterpret_cast<unsigned long long *>(sm + lay.cand);
+  AT *As = reinterpret_cast<AT *>(sm + lay.As);
+  const int kp = lay.kp;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t r0 = min(m, (int64_t)blockIdx.x * a.rows_per), r1 = min(m, r0 + a.rows_per);
+  const int64_t nrows = r1 - r0, ncache = min(nrows, a.rows_cached);
+  const AT *A = static_cast<const AT *>(a.A);
+  int par = 0;
+
+  // ---- set-up: this block's cached rows of A (asynchronous copies, all in flight at
+  //      once), identity column order, zero T, V corner and column flags
+  if (sizeof(AT) == 4 && a.vec4) {
+    const int64_t n4 = n / 4;
+    for (int64_t li = 0; li < ncache; ++li)
+      for (int64_t c4 = tid; c4 < n4; c4 += kCT) cp_async16(As + li * n + 4 * c4, A + (r0 + li) * a.lda + 4 * c4);
+  } else {
+    for (int64_t li = 0; li < ncache; ++li)
+      for (int64_t c = tid; c < n; c += kCT) cp_async_elem(As + li * n + c, A + (r0 + li) * a.lda + c);
+  }
+  for (int64_t c = tid; c < n; c += kCT) {
+    perm[c] = (int)c;
+    posof[c] = (int)c;
+  }
+  for (int lc = tid; lc < tm.nown; lc += kCT) {
+    flago[lc] = 0;
+    doneo[lc] = 0;
+  }
+  for (int q = tid; q < k * k; q += kCT) {
+    Ts[q] = 0.0;
+    Vt[q] = 0.0;
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
+
+  // ---- initial column norms and the first pivot
+  {
+    double *rp = red + (size_t)par * L;
+    ccolsum<AT, true>(a, As, ncache, r0, 0, nrows, ys, red4, rp);
+    for (int q = (int)n + tid; q < L; q += kCT) rp[q] = 0.0;
+    __syncthreads();
+    if (!allreduce(a, cl, tm, rp, svo, svs, par, &s_ok)) return cbail(a);
+    par ^= 1;
+    for (int lc = tid; lc < tm.nown; lc += kCT) {
+      vno[lc] = svo[lc];
+      vrefo[lc] = svo[lc];
+    }
+    __syncthreads();
+    choose_pivot(cl, tm, 0, n, vno, flago, doneo, perm, posof, cand, &s_res);
+  }
+
+  const double tol = sqrt(DBL_EPSILON);
+  for (int j = 0; j < k; ++j) {
+    const int c0 = perm[j];
+    const bool owner = j >= r0 && j < r1;
+    if (tid < j) {  // F[c0, :j] from the block that owns column c0
+      const double *pF = cl.map_shared_rank(Fo, (unsigned)(c0 % (int)tm.S));
+      s_f[tid] = pF[(int64_t)tid * no + c0 / (int)tm.S];
+    }
+    for (int lc = tid; lc < tm.nown; lc += kCT)  // A[j, :] of this block's columns, used after the reduction
+      ajo[lc] = (double)__ldg(A + (int64_t)j * a.lda + tm.rank + (int64_t)tm.S * lc);
+    __syncthreads();
+    // ---- rows: y = A[:, c0] - V[:, :j] F[c0, :j]^T (zero above row j)
+    double s2 = 0.0;
+    for (int64_t li = tid; li < nrows; li += kCT) {
+      const int64_t i = r0 + li;
+      double *vr = Vs + li * kp;
+      if (i < j) {
+        vr[j] = 0.0;
+        continue;
+      }
+      double y = li < ncache ? (double)As[li * n + c0] : (double)__ldg(A + i * a.lda + c0);
+      for (int l = 0; l < j; ++l) y = fma(-vr[l], s_f[l], y);
+      vr[j] = y;
+      s2 = fma(y, y, s2);
+      if constexpr (sizeof(AT) == 4) {
+        const float h = (float)y;
+        static_cast<float2 *>(ys)[li] = make_float2(h, (float)(y - (double)h));
+      } else {
+        static_cast<double *>(ys)[li] = y;
+      }
+    }
+    double *rp = red + (size_t)par * L;
+    red4[tid] = s2;
+    __syncthreads();
+    // V^T y over this block's rows below row j (j < 32): lanes = (row group g, column l)
+    // with the group width P the power of two >= j, so few FP64 lanes idle
+    if (j > 0) {
+      const int P = j <= 1 ? 1 : j <= 2 ? 2 : j <= 4 ? 4 : j <= 8 ? 8 : j <= 16 ? 16 : 32;
+      const int G = 32 / P, g = lane / P, l = lane % P;
+      double u = 0.0;
+      const int64_t lo = max((int64_t)0, (int64_t)j + 1 - r0);
+      for (int64_t li = lo + (int64_t)warp * G + g; li < nrows; li += (int64_t)kCW * G) {
+        const double *vr = Vs + li * kp;
+        if (l < j) u = fma(vr[l], vr[j], u);
+      }
+      for (int o = P; o < 32; o <<= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+      if (g == 0) red4[kCT + warp * 32 + l] = u;  // [0, kCT) holds the ||y||^2 partials
+    }
+    __syncthreads();
+    if (warp == 0) {  // ||y||^2 partial: 16 per lane in order, then the lanes
+      double t = 0.0;
+#pragma unroll
+      for (int q = 0; q < kCW; ++q) t += red4[lane * kCW + q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) {
+        rp[n + k] = t;
+        rp[n + k + 1] = owner ? Vs[(j - r0) * kp + j] : 0.0;
+      }
+    }
+    for (int q = tid - 32; q >= 0 && q < k; q += kCT) {  // warps 1..: V^T y and row j of V
+      double t = 0.0;
+      if (q < j)
+        for (int w = 0; w < kCW; ++w) t += red4[kCT + w * 32 + q];
+      rp[n + q] = t;
+      rp[n + k + 2 + q] = (owner && q < j) ? Vs[(j - r0) * kp + q] : 0.0;
+    }
+    // A^T y over this block's rows from row j on (its first barrier orders the above)
+    ccolsum<AT, false>(a, As, ncache, r0, max((int64_t)0, (int64_t)j - r0), nrows, ys, red4, rp);
+    if (!allreduce(a, cl, tm, rp, svo, svs, par, &s_ok)) return cbail(a);
+    par ^= 1;
+
+    // ---- reflector (one thread), then F[:, j], row j of R, norm downdates
+    if (tid == 0) {
+      const double x0 = svs[k + 1];
+      const double alpha = sqrt(svs[k]);
+      double tau = 0.0, beta = 0.0, v0 = 0.0;
+      if (alpha > 0.0) {
+        const double sg = (x0 < 0.0) ? -1.0 : 1.0;
+        v0 = x0 + sg * alpha;
+        tau = 2.0 / (2.0 * alpha * (alpha + fabs(x0)));
+        beta = -sg * alpha;
+      }
+      s_sc[0] = v0;
+      s_sc[1] = tau;
+      s_sc[2] = v0 - x0;
+      Vt[j * k + j] = v0;
+      if (owner) Vs[(j - r0) * kp + j] = v0;
+      if (blockIdx.x == 0) {
+        if (a.rdiag) a.rdiag[j] = beta;
+        if (a.piv) a.piv[j] = c0;
+      }
+    }
+    __syncthreads();
+    const double v0 = s_sc[0], tau = s_sc[1], dv = s_sc[2];
+    if (tid < j) {
+      const double vj = svs[k + 2 + tid];
+      Vt[j * k + tid] = vj;
+      su[tid] = fma(vj, v0, svs[tid]);  // V[:, l]^T v_j = sum below row j + V[j, l] v_jj
+    }
+    __syncthreads();
+    if (tid < j) {  // T(0:j, j) = -tau T(0:j, 0:j) u
+      double t = 0.0;
+      for (int q = tid; q < j; ++q) t = fma(Ts[tid * k + q], su[q], t);
+      Ts[tid * k + j] = -tau * t;
+    }
+    if (tid == 0) Ts[j * k + j] = tau;
+    for (int lc = tid - 64; lc >= 0 && lc < tm.nown; lc += kCT - 64) {  // warps 2..: this block's columns
+      if (doneo[lc]) continue;
+      const double ajc = ajo[lc];
+      const double w = fma(dv, ajc, svo[lc]);  // A^T v = A^T y + (v_jj - y_jj) A[j, :]
+      double corr = 0.0, rv = 0.0;
+      for (int l = 0; l < j; ++l) {
+        const double fl = Fo[(int64_t)l * no + lc];
+        corr = fma(fl, su[l], corr);
+        rv = fma(Vt[j * k + l], fl, rv);
+      }
+      const double f = tau * (w - corr);
+      Fo[(int64_t)j * no + lc] = f;
+      double r = ajc - rv;
+      r = fma(-v0, f, r);
+      double nv = vno[lc] - r * r;
+      const double ref = vrefo[lc];
+      if (ref > 0.0 && !(nv > tol * ref)) {
+        flago[lc] = 1;
+        nv = 0.0;
+      } else if (!(nv > 0.0)) {
+        nv = 0.0;
+      }
+      vno[lc] = nv;
+    }
+    __syncthreads();
+    if (j + 1 < k && choose_pivot(cl, tm, j + 1, n, vno, flago, doneo, perm, posof, cand, &s_res)) {
+      // exact norms of the flagged columns of the whole cluster (rare)
+      double *rq = red + (size_t)par * L;
+      for (int q = tid; q < L; q += kCT) rq[q] = 0.0;
+      __syncthreads();
+      for (unsigned q = 0; q < tm.S; ++q) {
+        const int *pf = cl.map_shared_rank(flago, q);
+        const double *pF = cl.map_shared_rank(Fo, q);
+        const int nq = (int)((n - (int64_t)q + tm.S - 1) / tm.S);
+        for (int lc = 0; lc < nq; ++lc) {
+          if (!pf[lc]) continue;
+          const int64_t c = q + (int64_t)tm.S * lc;
+          if (tid <= j) s_f[tid] = pF[(int64_t)tid * no + lc];
+          __syncthreads();
+          double t = 0.0;
+          for (int64_t li = max((int64_t)0, (int64_t)j + 1 - r0) + tid; li < nrows; li += kCT) {
+            double y = li < ncache ? (double)As[li * n + c] : (double)__ldg(A + (r0 + li) * a.lda + c);
+            const double *vr = Vs + li * kp;
+            for (int l = 0; l <= j; ++l) y = fma(-vr[l], s_f[l], y);
+            t = fma(y, y, t);
+          }
+          red4[tid] = t;
+          __syncthreads();
+          if (warp == 0) {
+            double u = 0.0;
+#pragma unroll
+            for (int w = 0; w < kCW; ++w) u += red4[lane * kCW + w];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+            if (lane == 0) rq[c] = u;
+          }
+          __syncthreads();
+        }
+      }
+      if (!allreduce(a, cl, tm, rq, svo, svs, par, &s_ok)) return cbail(a);
+      par ^= 1;
+      for (int lc = tid; lc < tm.nown; lc += kCT) {
+        if (flago[lc]) {
+          vno[lc] = svo[lc];
+          vrefo[lc] = svo[lc];
+          flago[lc] = 0;
+        }
+      }
+      __syncthreads();
+      choose_pivot(cl, tm, j + 1, n, vno, flago, doneo, perm, posof, cand, &s_res);
+    }
+  }
+
+  // ---- Q = [I_k; 0] - V (T V[0:k, :]^T) on this block's rows
+  for (int q = tid; q < k * k; q += kCT) {
+    const int l = q / k, cc = q % k;
+    double t = 0.0;
+    for (int p = l; p <= cc; ++p) t = fma(Ts[l * k + p], Vt[cc * k + p], t);
+    Ms[q] = t;
+  }
+  __syncthreads();
+  for (int64_t idx = tid; idx < nrows * k; idx += kCT) {
+    const int64_t li = idx / k, i = r0 + li;
+    const int cc = (int)(idx % k);
+    double t = (i == cc) ? 1.0 : 0.0;
+    const int lmax = (int)min((int64_t)k - 1, i);
+    const double *vr = Vs + li * kp;
+    for (int l = 0; l <= lmax; ++l) t = fma(-vr[l], Ms[l * k + cc], t);
+    a.Q[i * a.ldq + cc] = t;
+  }
+  cl.sync();  // no block leaves while a peer may still read its shared memory
+}
+
+// ---- host side: per-device limits, cached
+struct DevInfo {
+  bool init = false;
+  int smem_dyn = 0;          // dynamic shared memory one block may use
+  int max_clusters[5] = {};  // for cluster sizes 16, 8, 4, 2, 1 (one block per SM)
+  bool coop_cluster_ok = true;
+};
+constexpr int kSizes[5] = {16, 8, 4, 2, 1};
+constexpr int kMaxDev = 64;
+std::mutex g_mu;
+DevInfo g_info[2][kMaxDev];  // [FP32 A, FP64 A]
+
+template <typename AT>
+bool dev_info(int dev, DevInfo **out) {
+  if (dev < 0 || dev >= kMaxDev) return false;
+  std::lock_guard<std::mutex> lock(g_mu);
+  DevInfo &d = g_info[sizeof(AT) == 8][dev];
+  if (!d.init) {
+    int optin = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
+    auto kern = qrp_cluster_kernel<AT>;
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return false;
+    const int dyn = optin - (int)fa.sharedSizeBytes;
+    if (dyn <= 0) return false;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) != cudaSuccess) return false;
+    const bool big_ok = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
+    cudaGetLastError();
+    for (int si = 0; si < 5; ++si) {
+      const int S = kSizes[si];
+      d.max_clusters[si] = 0;
+      if (S > 8 && !big_ok) continue;
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = (unsigned)S;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3((unsigned)S);
+      cfg.blockDim = dim3(kCT);
+      cfg.dynamicSmemBytes = (size_t)dyn;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int nc = 0;
+      if (cudaOccupancyMaxActiveClusters(&nc, kern, &cfg) == cudaSuccess) d.max_clusters[si] = nc;
+      cudaGetLastError();
+    }
+    d.smem_dyn = dyn;
+    d.init = true;
+  }
+  *out = &d;
+  return true;
+}
+
+const char *qrp_form_env() {
+  const char *e = std::getenv("TUCKER_QRP_FORM");
+  return e ? e : "";
+}
+
+}  // namespace
+
+// Runs the cluster form when its shared-memory plan fits; false = not applicable
+// (the caller runs another form).  *err reports a failed launch that was attempted.
+template <typename AT>
+bool qrp_cluster(const AT *A, int64_t m, int64_t n, int64_t lda, int k, double *Q, int64_t ldq, int64_t *piv,
+                 double *rdiag, QrpWork *w, cudaStream_t s, cudaError_t *err) {
+  *err = cudaSuccess;
+  if (std::strcmp(qrp_form_env(), "persistent") == 0 || std::strcmp(qrp_form_env(), "multi") == 0) return false;
+  if (k < 1 || k > 32 || m < 1 || n < 1 || n > (1 << 20)) return false;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  DevInfo *d = nullptr;
+  if (!dev_info<AT>(dev, &d)) return false;
+  const int L = (int)n + 2 * k + 2;
+  const int es = (int)sizeof(AT);
+  const size_t avail = (size_t)d->smem_dyn;
+  int S = 0, C = 0;
+  int64_t rows_per = 0, rows_cached = 0;
+  auto need = [&](int s_, int64_t rp, int64_t rc) { return clayout(n, k, L, s_, rp, rc, es).total; };
+  // one cluster holding all of A in shared memory: no grid-wide barrier
+  for (int si = 0; si < 2 && !S; ++si) {
+    if (d->max_clusters[si] < 1) continue;
+    const int64_t rp = (m + kSizes[si] - 1) / kSizes[si];
+    if (need(kSizes[si], rp, rp) <= avail) {
+      S = kSizes[si];
+      C = 1;
+      rows_per = rows_cached = rp;
+    }
+  }
+  if (!S) {
+    if (!d->coop_cluster_ok) return false;
+    // every block adds up C cluster sums per step: take the largest cluster size that
+    // keeps at least 90% of the blocks that fit with any size
+    int gmax = 0;
+    for (int si = 1; si < 4; ++si) gmax = std::max(gmax, kSizes[si] * d->max_clusters[si]);
+    if (gmax < 2) return false;
+    for (int si = 1; si < 4 && !S; ++si) {
+      if (10 * kSizes[si] * d->max_clusters[si] >= 9 * gmax) {
+        S = kSizes[si];
+        C = d->max_clusters[si];
+      }
+    }
+    rows_per = (m + (int64_t)S * C - 1) / ((int64_t)S * C);
+    const size_t base = need(S, rows_per, 0);
+    if (base > avail) return false;
+    rows_cached = std::min<int64_t>(rows_per, (int64_t)((avail - base) / ((size_t)n * es + 16)));
+    while (rows_cached > 0 && need(S, rows_per, rows_cached) > avail) --rows_cached;
+  }
+  const size_t smem = need(S, rows_per, rows_cached);
+  if (C > 1 && 2 * (size_t)C * L > w->part_elems) return false;  // the cluster sums live in `part`
+
+  CArgs a{};
+  a.A = A;
+  a.m = m;
+  a.n = n;
+  a.lda = lda;
+  a.k = k;
+  a.L = L;
+  a.nclusters = C;
+  a.vec4 = (es == 4 && n % 4 == 0 && lda % 4 == 0 && (reinterpret_cast<uintptr_t>(A) % 16) == 0) ? 1 : 0;
+  a.rows_per = rows_per;
+  a.rows_cached = rows_cached;
+  a.slots = w->part;
+  a.bar = w->bar;
+  a.err = w->err_out ? w->err_out : w->bar + 2;
+  a.Q = Q;
+  a.ldq = ldq;
+  a.piv = piv;
+  a.rdiag = rdiag;
+  if (C > 1 && (*err = cudaMemsetAsync(w->bar, 0, 3 * sizeof(unsigned), s)) != cudaSuccess) return true;
+
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[2];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)S;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  int nat = 1;
+  if (C > 1) {  // the clusters wait on one another: all of them must be resident
+    at[1].id = cudaLaunchAttributeCooperative;
+    at[1].val.cooperative = 1;
+    nat = 2;
+  }
+  cfg.gridDim = dim3((unsigned)(S * C));
+  cfg.blockDim = dim3(kCT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = at;
+  cfg.numAttrs = nat;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, qrp_cluster_kernel<AT>, a);
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // a configuration error is not sticky
+    if (C > 1) {
+      std::lock_guard<std::mutex> lock(g_mu);
+      d->coop_cluster_ok = false;
+    }
+    return false;
+  }
+  ::tk::count_launch();
+  return true;
+}
+
+template bool qrp_cluster<float>(const float *, int64_t, int64_t, int64_t, int, double *, int64_t, int64_t *,
+                                 double *, QrpWork *, cudaStream_t, cudaError_t *);
+template bool qrp_cluster<double>(const double *, int64_t, int64_t, int64_t, int, double *, int64_t, int64_t *,
+                                  double *, QrpWork *, cudaStream_t, cudaError_t *);
+
+}  // namespace tk

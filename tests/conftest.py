@@ -17,3 +17,12 @@ def pytest_configure(config):
 @pytest.fixture(scope="session")
 def golden_dir():
     return GOLDEN
+
+
+@pytest.fixture(params=["cluster", "persistent"])
+def qrp_form(request, monkeypatch):
+    """Runs a test with each single-launch form of the QRP: the cluster form (one grid
+    barrier per reflector; the default wherever its shared-memory plan fits) and the
+    persistent cooperative form (two grid barriers per reflector)."""
+    monkeypatch.setenv("TUCKER_QRP_FORM", request.param)
+    return request.param

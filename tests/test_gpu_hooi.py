@@ -34,13 +34,13 @@ def check_against_oracle(w, iters, fit_tol=1e-6, **kw):
     return fits, ref
 
 
-def test_hooi_tiny_config_matches_oracle():
+def test_hooi_tiny_config_matches_oracle(qrp_form):
     w = synth.make("tiny-100^3")
     fits, ref = check_against_oracle(w, w.workload.iters)
     assert all(0.0 <= f <= 1.0 for f in fits)
 
 
-def test_hooi_order4_fat_mode_gram_and_direct():
+def test_hooi_order4_fat_mode_gram_and_direct(qrp_form):
     # last mode 40 < P = 8*8*8 = 512: the paper's Gram branch; direct QRP as a flag
     rng = np.random.default_rng(2)
     wl = synth.Workload("order4-small", (300, 250, 200, 40), 60_000, (8, 8, 8, 8), 3, 77, (("uniform",),) * 4,
@@ -64,8 +64,14 @@ def test_hooi_exact_low_rank_recovery():
     assert np.linalg.norm(Xh - X) / np.linalg.norm(X) < 1e-5
 
 
-def test_hooi_zipf_small_matches_oracle():
+def test_hooi_zipf_small_matches_oracle(qrp_form):
     w = synth.make("zipf-10k^3", nnz=100_000)
+    check_against_oracle(w, 2)
+
+
+def test_hooi_skew_recipe_small_matches_oracle(qrp_form):
+    # the 50,000 x 50,000 x 1,000 shape at 300k nonzeros: FP32 unfoldings of 50,000 x 256
+    w = synth.make("skew-20M", nnz=300_000)
     check_against_oracle(w, 2)
 
 

@@ -37,8 +37,8 @@ def min_pivot_gap(A, k):
 
 
 @pytest.mark.parametrize("m,n,k", [(500, 64, 16), (3000, 256, 16), (64, 64, 64), (257, 33, 8), (40, 300, 20),
-                                   (1, 5, 1), (6, 1, 1)])
-def test_qrp_matches_oracle(m, n, k):
+                                   (1, 5, 1), (6, 1, 1), (1000, 256, 16), (20_000, 256, 16), (9_001, 130, 12)])
+def test_qrp_matches_oracle(m, n, k, qrp_form):
     rng = np.random.default_rng(m * 1000 + n + k)
     A = rng.standard_normal((m, n)) * rng.uniform(0.2, 5.0, n)
     Q, piv, rd = gpu_qrp(A, k)
@@ -50,7 +50,7 @@ def test_qrp_matches_oracle(m, n, k):
     np.testing.assert_allclose(Q.T @ Q, np.eye(k), atol=1e-13)
 
 
-def test_qrp_rank_deficient_and_zero_columns():
+def test_qrp_rank_deficient_and_zero_columns(qrp_form):
     rng = np.random.default_rng(3)
     A = rng.standard_normal((200, 3)) @ rng.standard_normal((3, 40))
     A[:, 5] = 0.0
@@ -64,7 +64,7 @@ def test_qrp_rank_deficient_and_zero_columns():
     np.testing.assert_allclose(Q[:, :3] @ (Q[:, :3].T @ A), A, atol=1e-9 * np.abs(A).max())
 
 
-def test_qrp_all_zero_matrix():
+def test_qrp_all_zero_matrix(qrp_form):
     Q, piv, rd = gpu_qrp(np.zeros((30, 7)), 4)
     np.testing.assert_array_equal(rd, 0.0)
     np.testing.assert_allclose(Q, np.eye(30)[:, :4], atol=0)
@@ -80,9 +80,9 @@ def test_qrp_rejects_bad_sizes():
                       work=torch.empty(64, dtype=torch.uint8, device="cuda"))
 
 
-def test_qrp_runs_as_one_persistent_launch():
-    """Factorisations with n <= 8192 run as one cooperative launch (the multi-kernel
-    form, kept for wider matrices, launches 3k + 3 kernels)."""
+def test_qrp_runs_as_one_launch(qrp_form):
+    """Factorisations with n <= 8192 run as one launch in either single-launch form (the
+    multi-kernel form, kept for wider matrices, launches 3k + 3 kernels)."""
     T = lib()
     rng = np.random.default_rng(5)
     for m, n, k in [(50_000, 256, 16), (1000, 256, 16), (40, 6, 4)]:
@@ -93,3 +93,17 @@ def test_qrp_runs_as_one_persistent_launch():
         T.qrp_leading(A, k)
         torch.cuda.synchronize()
         assert T.tucker_kernel_launches() - before == 1, (m, n, k)
+
+
+def test_qrp_cluster_form_on_a_tall_unfolding():
+    """50,000 x 256, k = 16 (the shape of a 20M-nonzero tensor's large-mode unfolding):
+    several clusters, rows partly in shared memory; the two forms pick the same pivots
+    and agree on Q and R to rounding."""
+    rng = np.random.default_rng(50)
+    A = rng.standard_normal((50_000, 256)) * rng.uniform(0.2, 5.0, 256)
+    ref = oracle.qrp(A, 16)
+    assert min_pivot_gap(A, 16) > 1e-10
+    Q, piv, rd = gpu_qrp(A, 16)
+    np.testing.assert_array_equal(piv, ref.piv)
+    np.testing.assert_allclose(rd, ref.rdiag, rtol=1e-11)
+    np.testing.assert_allclose(Q, ref.Q, atol=1e-11)
