@@ -114,7 +114,7 @@ static tucker_status init_impl(Ctx *c, const uint32_t *coords, const float *vals
   for (int n = 0; n < N; ++n) {
     const ModeCopy &mc = c->mode[n];
     ymax = std::max(ymax, mc.I * mc.P);
-    carry_max = std::max(carry_max, mc.n_units * mc.P);
+    carry_max = std::max(carry_max, std::max(mc.n_units, mc.fn_units) * mc.P);
     Imax = std::max(Imax, mc.I);
     IRmax = std::max(IRmax, c->dims[n] * c->ranks[n]);
     const int ncols = qrp_n_cols(c, n);

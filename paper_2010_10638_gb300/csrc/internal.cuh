@@ -43,7 +43,23 @@ struct ModeCopy {
   int64_t n_long = 0;
   uint32_t *src = nullptr;             // [nnz] coalesced (lexicographic) index of sorted position e;
                                        // nullptr for mode 1, whose order is the lexicographic one
+  // Fiber level (order 3): within a slice, runs of nonzeros with the same index of the
+  // first remaining mode, cut every kFiberCap nonzeros.  Work units and long-slice tables
+  // over fibers, as above over nonzeros.
+  bool fib = false;
+  int64_t F = 0;                       // fibers
+  uint32_t *fptr = nullptr;            // [F+1] first sorted position of each fiber
+  uint32_t *fmid = nullptr;            // [F] index of the first remaining mode of each fiber
+  uint32_t *fsptr = nullptr;           // [S+1] first fiber of each non-empty slice
+  int fchunk = 0;
+  uint32_t *funit_e0 = nullptr, *funit_k0 = nullptr;
+  int32_t *funit_slot = nullptr;
+  int64_t fn_units = 0;
+  uint32_t *flong_k = nullptr, *flong_u0 = nullptr, *flong_np = nullptr;
+  int64_t fn_long = 0;
 };
+
+constexpr int kFiberCap = 32;  // nonzeros per fiber at most (longer runs are cut)
 
 // Workspace of the QR with column pivoting (one set, sized for the largest mode).
 struct QrpWork {

@@ -14,6 +14,7 @@
 //     rows are combined by a second pass.
 #include <algorithm>
 #include <cstdlib>
+#include <cstring>
 
 #include "internal.cuh"
 
@@ -348,6 +349,45 @@ __global__ void compact_kernel(int64_t n, const uint32_t *flag, const uint32_t *
     if (flag[i]) out[pos[i]] = (uint32_t)i;
 }
 
+// ---- fibers (order 3): runs of one slice with the same index of the first remaining
+//      mode (the middle level of a CSF tree), cut every kFiberCap nonzeros
+__global__ void fiber_flag_kernel(int64_t n, const uint32_t *row, const uint32_t *mid, uint32_t *flag) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    flag[e] = (e == 0 || row[e] != row[e - 1] || mid[e] != mid[e - 1]) ? 1u : 0u;
+}
+
+__global__ void fiber_nstart_kernel(int64_t n, const uint32_t *flag, const uint32_t *pos, uint32_t *nstart) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    if (flag[e]) nstart[pos[e]] = (uint32_t)e;
+}
+
+__global__ void fiber_cut_kernel(int64_t n, const uint32_t *flag, const uint32_t *pos, const uint32_t *nstart,
+                                 uint32_t cap, uint32_t *cut) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t fid = pos[e] + flag[e] - 1u;  // the run that contains e
+    cut[e] = (((uint32_t)e - nstart[fid]) % cap == 0u) ? 1u : 0u;
+  }
+}
+
+__global__ void fiber_write_kernel(int64_t n, const uint32_t *cut, const uint32_t *cpos, const uint32_t *mid,
+                                   uint32_t *fptr, uint32_t *fmid, int64_t F) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    if (cut[e]) {
+      fptr[cpos[e]] = (uint32_t)e;
+      fmid[cpos[e]] = mid[e];
+    }
+    if (e == 0) fptr[F] = (uint32_t)n;
+  }
+}
+
+__global__ void fiber_slices_kernel(int64_t S, const uint32_t *sptr, const uint32_t *cpos, uint32_t *fsptr,
+                                    int64_t F) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < S; k += (int64_t)gridDim.x * blockDim.x) {
+    fsptr[k] = cpos[sptr[k]];  // a slice start is always a fiber start
+    if (k == 0) fsptr[S] = (uint32_t)F;
+  }
+}
+
 // units contributed by each non-empty slice k: pieces of a long slice, or 1 for the
 // first slice of a run of short slices (a new run starts at a long slice, after a long
 // slice, and where the slice start crosses into a new multiple of `chunk`).
@@ -441,6 +481,58 @@ static tucker_status read_u32(Ctx *c, const uint32_t *d, uint32_t *h, cudaStream
   return TUCKER_OK;
 }
 
+// Work units over a slice table `ptr` ([S+1] offsets into positions: nonzeros or fibers).
+struct UnitTables {
+  uint32_t **e0, **k0, **long_k, **long_u0, **long_np;
+  int32_t **slot;
+  int64_t *n_units, *n_long;
+};
+
+static tucker_status build_units(Ctx *c, int64_t S, const uint32_t *ptr, int chunk, uint32_t *nu, uint32_t *islong,
+                                 uint32_t *uoff, uint32_t *lid, uint32_t *stmp, uint32_t *d_small, UnitTables o,
+                                 cudaStream_t s) {
+  uint32_t nunits = 0, nlong = 0;
+  if (S > 0) {
+    unit_count_kernel<<<grid_for(S), 256, 0, s>>>(S, ptr, (uint32_t)chunk, nu, islong);
+    ::tk::count_launch();
+    exclusive_scan_total(nu, uoff, S, stmp, d_small + 2, s);
+    exclusive_scan_total(islong, lid, S, stmp, d_small + 3, s);
+    uint32_t h2[2];
+    TK_TRY(cudaMemcpyAsync(h2, d_small + 2, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    TK_TRY(cudaStreamSynchronize(s));
+    nunits = h2[0];
+    nlong = h2[1];
+  }
+  *o.n_units = nunits;
+  *o.n_long = nlong;
+  TK_TRY(dev_alloc(c, o.e0, (size_t)std::max<uint32_t>(nunits, 1)));
+  TK_TRY(dev_alloc(c, o.k0, (size_t)std::max<uint32_t>(nunits, 1)));
+  TK_TRY(dev_alloc(c, o.slot, (size_t)std::max<uint32_t>(nunits, 1)));
+  TK_TRY(dev_alloc(c, o.long_k, (size_t)std::max<uint32_t>(nlong, 1)));
+  TK_TRY(dev_alloc(c, o.long_u0, (size_t)std::max<uint32_t>(nlong, 1)));
+  TK_TRY(dev_alloc(c, o.long_np, (size_t)std::max<uint32_t>(nlong, 1)));
+  if (S > 0) {
+    unit_write_kernel<<<grid_for(S), 256, 0, s>>>(S, ptr, (uint32_t)chunk, nu, uoff, islong, lid, *o.e0, *o.k0,
+                                                   *o.slot, *o.long_k, *o.long_u0, *o.long_np);
+    ::tk::count_launch();
+  }
+  TK_TRY(cudaGetLastError());
+  return TUCKER_OK;
+}
+
+// Whether mode copies of order-3 tensors get a fiber level (TUCKER_TTMC_FIBERS): "1"
+// always, "auto" when the fibers are at most kFiberShare of the nonzeros, otherwise never.
+// Off by default: on the 20M-nonzero skewed workload the fiber form, although it does
+// 2-4x fewer multiply-adds, ran slower than the nonzero form in every mode (its tiles
+// chain more dependent loads, and the Zipf-skewed fiber lengths leave lanes idle).
+static int fiber_policy() {
+  const char *f = std::getenv("TUCKER_TTMC_FIBERS");
+  if (f && std::strcmp(f, "1") == 0) return 1;
+  if (f && std::strcmp(f, "auto") == 0) return -1;
+  return 0;
+}
+constexpr double kFiberShare = 0.6;
+
 tucker_status build_sorted_copies(Ctx *c, const uint32_t *coords_in, const float *vals_in, cudaStream_t s) {
   const int N = c->N;
   const int64_t n_in = c->nnz_in;
@@ -527,6 +619,12 @@ tucker_status build_sorted_copies(Ctx *c, const uint32_t *coords_in, const float
   TK_TRY(tmp.get(&islong, std::max<int64_t>(Z, 1) + 1));
   TK_TRY(tmp.get(&uoff, std::max<int64_t>(Z, 1) + 1));
   TK_TRY(tmp.get(&lid, std::max<int64_t>(Z, 1) + 1));
+  uint32_t *fnstart = nullptr, *fcut = nullptr, *fcpos = nullptr;
+  if (N == 3 && fiber_policy() != 0) {
+    TK_TRY(tmp.get(&fnstart, std::max<int64_t>(Z, 1)));
+    TK_TRY(tmp.get(&fcut, std::max<int64_t>(Z, 1)));
+    TK_TRY(tmp.get(&fcpos, std::max<int64_t>(Z, 1)));
+  }
   for (int n = 0; n < N; ++n) {
     ModeCopy &mc = c->mode[n];
     mc.I = c->dims[n];
@@ -594,32 +692,60 @@ tucker_status build_sorted_copies(Ctx *c, const uint32_t *coords_in, const float
       ::tk::count_launch();
     }
     // work units
-    uint32_t nunits = 0, nlong = 0;
-    if (S > 0) {
-      unit_count_kernel<<<grid_for(S), 256, 0, s>>>(S, mc.sptr, (uint32_t)mc.chunk, nu, islong);
-      ::tk::count_launch();
-      exclusive_scan_total(nu, uoff, S, stmp, d_small + 2, s);
-      exclusive_scan_total(islong, lid, S, stmp, d_small + 3, s);
-      uint32_t h2[2];
-      TK_TRY(cudaMemcpyAsync(h2, d_small + 2, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-      TK_TRY(cudaStreamSynchronize(s));
-      nunits = h2[0];
-      nlong = h2[1];
+    {
+      UnitTables o{&mc.unit_e0, &mc.unit_k0, &mc.long_k, &mc.long_u0, &mc.long_np, &mc.unit_slot, &mc.n_units,
+                   &mc.n_long};
+      tucker_status st2 = build_units(c, S, mc.sptr, mc.chunk, nu, islong, uoff, lid, stmp, d_small, o, s);
+      if (st2 != TUCKER_OK) return st2;
     }
-    mc.n_units = nunits;
-    mc.n_long = nlong;
-    TK_TRY(dev_alloc(c, &mc.unit_e0, (size_t)std::max<uint32_t>(nunits, 1)));
-    TK_TRY(dev_alloc(c, &mc.unit_k0, (size_t)std::max<uint32_t>(nunits, 1)));
-    TK_TRY(dev_alloc(c, &mc.unit_slot, (size_t)std::max<uint32_t>(nunits, 1)));
-    TK_TRY(dev_alloc(c, &mc.long_k, (size_t)std::max<uint32_t>(nlong, 1)));
-    TK_TRY(dev_alloc(c, &mc.long_u0, (size_t)std::max<uint32_t>(nlong, 1)));
-    TK_TRY(dev_alloc(c, &mc.long_np, (size_t)std::max<uint32_t>(nlong, 1)));
-    if (S > 0) {
-      unit_write_kernel<<<grid_for(S), 256, 0, s>>>(S, mc.sptr, (uint32_t)mc.chunk, nu, uoff, islong, lid, mc.unit_e0,
-                                                     mc.unit_k0, mc.unit_slot, mc.long_k, mc.long_u0, mc.long_np);
+    // fiber level (order 3)
+    const int fp = fiber_policy();
+    if (N == 3 && Z > 0 && S > 0 && fp != 0) {
+      fiber_flag_kernel<<<grid_for(Z), 256, 0, s>>>(Z, row, mc.idx[0], flag);
       ::tk::count_launch();
+      exclusive_scan_total(flag, pos, Z, stmp, d_small + 4, s);
+      fiber_nstart_kernel<<<grid_for(Z), 256, 0, s>>>(Z, flag, pos, fnstart);
+      ::tk::count_launch();
+      uint32_t cap = (uint32_t)kFiberCap;
+      if (const char *fc = std::getenv("TUCKER_TTMC_FIBER_CAP")) {
+        const int v = std::atoi(fc);
+        if (v >= 1 && v <= kFiberCap) cap = (uint32_t)v;
+      }
+      fiber_cut_kernel<<<grid_for(Z), 256, 0, s>>>(Z, flag, pos, fnstart, cap, fcut);
+      ::tk::count_launch();
+      exclusive_scan_total(fcut, fcpos, Z, stmp, d_small + 5, s);
+      uint32_t F = 0;
+      tucker_status st2 = read_u32(c, d_small + 5, &F, s);
+      if (st2 != TUCKER_OK) return st2;
+      if (fp == 1 || (double)F <= kFiberShare * (double)Z) {
+        mc.fib = true;
+        mc.F = F;
+        TK_TRY(dev_alloc(c, &mc.fptr, (size_t)F + 1));
+        TK_TRY(dev_alloc(c, &mc.fmid, (size_t)std::max<uint32_t>(F, 1)));
+        TK_TRY(dev_alloc(c, &mc.fsptr, (size_t)S + 1));
+        fiber_write_kernel<<<grid_for(Z), 256, 0, s>>>(Z, fcut, fcpos, mc.idx[0], mc.fptr, mc.fmid, F);
+        ::tk::count_launch();
+        fiber_slices_kernel<<<grid_for(S), 256, 0, s>>>(S, mc.sptr, fcpos, mc.fsptr, F);
+        ::tk::count_launch();
+        TK_TRY(cudaGetLastError());
+        // a fiber unit spans about as many nonzeros as a nonzero unit (a fiber costs its
+        // nonzeros plus one rank-1 update), in multiples of 32 fibers
+        {
+          const double per = (double)mc.chunk * (double)F / (double)Z;
+          int fc = (int)(per / 32.0) * 32;
+          mc.fchunk = std::max(64, std::min(2048, fc));
+          const char *f = std::getenv("TUCKER_TTMC_FCHUNK");
+          if (f) {
+            const int v = std::atoi(f);
+            if (v >= 32 && v <= (1 << 20) && (v % 32) == 0) mc.fchunk = v;
+          }
+        }
+        UnitTables o{&mc.funit_e0, &mc.funit_k0, &mc.flong_k, &mc.flong_u0, &mc.flong_np, &mc.funit_slot,
+                     &mc.fn_units, &mc.fn_long};
+        st2 = build_units(c, S, mc.fsptr, mc.fchunk, nu, islong, uoff, lid, stmp, d_small, o, s);
+        if (st2 != TUCKER_OK) return st2;
+      }
     }
-    TK_TRY(cudaGetLastError());
   }
   TK_TRY(cudaStreamSynchronize(s));
   return TUCKER_OK;

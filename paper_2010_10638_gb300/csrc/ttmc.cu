@@ -44,6 +44,8 @@ struct TtmcParams {
   float *Y;
   float *carry;
   int64_t P;
+  const uint32_t *fptr;  // fiber form: [F+1] first nonzero of each fiber (positions above are fibers)
+  const uint32_t *fmid;  // fiber form: [F] index of the first remaining mode of each fiber
 };
 
 // Slice structure of the tile [e, e + nt) of sorted positions, kb = slice of position e.
@@ -390,6 +392,185 @@ __global__ void __launch_bounds__(kTtmcWarps * 32) ttmc_pipe_kernel(const TtmcPa
     x = xn;
     ia = ian;
     ib = ibn;
+  }
+}
+
+// ============================================================================ fiber form
+// Order 3 with a fiber level (Section III-C, CSF): within a slice, the nonzeros that
+// share the index i_a of the first remaining mode form a fiber f (cut every kFiberCap
+// nonzeros), and the fiber contributes U_a(i_a, :) t_f^T with
+//     t_f = sum over its nonzeros of x_z U_b(i_b(z), :),
+// so the RB-term sum is formed once per nonzero and the PL x RB rank-1 update once per
+// fiber.  Work units, slice offsets and long-slice pieces count fibers.  Per tile of 32
+// fibers the warp
+//   1. forms t_f with QL = RB / 4 lanes per fiber (lane s of the group owns
+//      t_f[4s, 4s+4)); group q holds the fibers q, q + 32/QL, ... of the tile and walks
+//      them side by side, UN nonzeros of each per step, so every factor-row load is one
+//      contiguous row per group and QL * UN rows per lane are in flight;
+//   2. stages U_a(i_a, :) and t_f in shared memory and accumulates the slice segments
+//      exactly as the nonzero form does.
+// Fiber offsets and middle indices of tile t+1 are prefetched during tile t.
+template <int PL, int RB, int TA, int TB>
+__global__ void __launch_bounds__(kTtmcWarps * 32) ttmc_fiber_kernel(const TtmcParams p) {
+  constexpr int G = (PL / TA) * (RB / TB);
+  constexpr int NG = 32 / G;
+  constexpr int QL = RB / 4;   // lanes per fiber in step 1
+  constexpr int FP = 32 / QL;  // fibers per group pass
+  constexpr int UN = RB >= 32 ? 1 : 2;  // nonzeros of each fiber per step
+  static_assert(G * NG == 32, "group size must divide the warp");
+  static_assert(PL % 4 == 0 && RB % 4 == 0 && QL <= 32 && 32 % QL == 0, "16-byte row pieces");
+  extern __shared__ float4 smem_f4[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float *xa = reinterpret_cast<float *>(smem_f4) + w * 32 * (PL + RB);
+  float *bb = xa + 32 * PL;
+  const int64_t u = (int64_t)blockIdx.x * kTtmcWarps + w;
+  if (u >= p.n_units) return;
+  const float *UA = static_cast<const float *>(p.U[0]);
+  const float *UB = static_cast<const float *>(p.U[1]);
+  const uint32_t *idxB = p.idx[1];
+  const uint32_t f0 = __ldg(p.unit_e0 + u);
+  const uint32_t f_end = (u + 1 < p.n_units) ? __ldg(p.unit_e0 + u + 1) : p.Z;
+  const int slot = __ldg(p.unit_slot + u);
+  const int ntiles = (int)((f_end - f0 + 31u) / 32u);
+  const int g = lane / G, j = lane % G;
+  const int ra0 = (j / (RB / TB)) * TA, rb0 = (j % (RB / TB)) * TB;
+  const int fq = lane / QL, s = lane % QL;
+  float acc[TA][TB];
+#pragma unroll
+  for (int a = 0; a < TA; ++a)
+#pragma unroll
+    for (int b = 0; b < TB; ++b) acc[a][b] = 0.f;
+
+  uint32_t kb = __ldg(p.unit_k0 + u);
+  // fiber bounds and middle index of lane's fiber in tile 0 (later tiles: prefetched)
+  uint32_t zb = 0u, ze = 0u, im = 0u;
+  if (f0 + lane < f_end) {
+    zb = __ldg(p.fptr + f0 + lane);
+    ze = __ldg(p.fptr + f0 + lane + 1);
+    im = __ldg(p.fmid + f0 + lane);
+  }
+  for (int t = 0; t < ntiles; ++t) {
+    const uint32_t e = f0 + 32u * (uint32_t)t;
+    const int nt = (int)min(32u, f_end - e);
+    const TileSlices ts = tile_slices(p.sptr, p.S, kb, e, nt, lane);
+    uint32_t zbn = 0u, zen = 0u, imn = 0u;
+    if (e + 32u + (uint32_t)lane < f_end) {
+      zbn = __ldg(p.fptr + e + 32u + lane);
+      zen = __ldg(p.fptr + e + 33u + lane);
+      imn = __ldg(p.fmid + e + 32u + lane);
+    }
+    // 1. t_f: this group's QL fibers side by side
+    uint32_t zc[QL], zn[QL];
+#pragma unroll
+    for (int k = 0; k < QL; ++k) {
+      const int fl = k * FP + fq;
+      const uint32_t b0 = __shfl_sync(kFull, zb, fl), b1 = __shfl_sync(kFull, ze, fl);
+      zc[k] = b0;
+      zn[k] = (fl < nt) ? b1 : b0;
+    }
+    float4 tq[QL];
+#pragma unroll
+    for (int k = 0; k < QL; ++k) tq[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    bool more = false;
+#pragma unroll
+    for (int k = 0; k < QL; ++k) more |= zc[k] < zn[k];
+    while (__any_sync(kFull, more)) {
+      float xv[QL][UN];
+      uint32_t iv[QL][UN];
+#pragma unroll
+      for (int k = 0; k < QL; ++k)
+#pragma unroll
+        for (int v = 0; v < UN; ++v) {
+          const uint32_t z = zc[k] + (uint32_t)v;
+          const bool ok = z < zn[k];
+          xv[k][v] = ok ? __ldg(p.val + z) : 0.f;
+          iv[k][v] = ok ? __ldg(idxB + z) : 0xffffffffu;
+        }
+      float4 r[QL][UN];
+#pragma unroll
+      for (int k = 0; k < QL; ++k)
+#pragma unroll
+        for (int v = 0; v < UN; ++v)
+          r[k][v] = iv[k][v] != 0xffffffffu
+                        ? __ldg(reinterpret_cast<const float4 *>(UB + (size_t)iv[k][v] * RB) + s)
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
+      more = false;
+#pragma unroll
+      for (int k = 0; k < QL; ++k) {
+#pragma unroll
+        for (int v = 0; v < UN; ++v) {
+          tq[k].x = fmaf(xv[k][v], r[k][v].x, tq[k].x);
+          tq[k].y = fmaf(xv[k][v], r[k][v].y, tq[k].y);
+          tq[k].z = fmaf(xv[k][v], r[k][v].z, tq[k].z);
+          tq[k].w = fmaf(xv[k][v], r[k][v].w, tq[k].w);
+        }
+        zc[k] += UN;
+        more |= zc[k] < zn[k];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < QL; ++k)  // zero rows past the tile's fibers
+      *reinterpret_cast<float4 *>(bb + (k * FP + fq) * RB + 4 * s) = tq[k];
+    // 2. the middle rows U_a(i_a, :), then the slice segments
+#pragma unroll
+    for (int it = lane; it < 32 * (PL / 4); it += 32) {
+      const int tt = it / (PL / 4), c = (it % (PL / 4)) * 4;
+      const uint32_t r = __shfl_sync(kFull, im, tt);
+      if (tt < nt)
+        *reinterpret_cast<float4 *>(xa + tt * PL + c) = __ldg(reinterpret_cast<const float4 *>(UA + (size_t)r * PL + c));
+    }
+    __syncwarp();
+    // slice segments of the tile
+    uint32_t segs = ts.starts | 1u;
+    while (segs) {
+      const int p0 = __ffs(segs) - 1;
+      segs &= segs - 1u;
+      const int p1 = segs ? (__ffs(segs) - 1) : nt;
+      int qq = p0 + g;
+      auto step = [&](int r) {
+        float av[TA], bv[TB];
+        lds<TA>(xa + r * PL + ra0, av);
+        lds<TB>(bb + r * RB + rb0, bv);
+#pragma unroll
+        for (int a = 0; a < TA; ++a)
+#pragma unroll
+          for (int b = 0; b < TB; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+      };
+      for (; qq + NG < p1; qq += 2 * NG) {
+        step(qq);
+        step(qq + NG);
+      }
+      if (qq < p1) step(qq);
+      const bool flush = (p1 < nt) || ts.end_is_start || (e + (uint32_t)nt == f_end);
+      if (flush) {
+#pragma unroll
+        for (int o = G; o < 32; o <<= 1)
+#pragma unroll
+          for (int a = 0; a < TA; ++a)
+#pragma unroll
+            for (int b = 0; b < TB; ++b) acc[a][b] += __shfl_xor_sync(kFull, acc[a][b], o);
+        const uint32_t kseg = __shfl_sync(kFull, ts.kp, p0);
+        if (g == 0) {
+          float *dst = (slot >= 0) ? p.carry + (size_t)slot * p.P : p.Y + (size_t)__ldg(p.sid + kseg) * p.P;
+#pragma unroll
+          for (int a = 0; a < TA; ++a) {
+            float *d = dst + (size_t)(ra0 + a) * RB + rb0;
+#pragma unroll
+            for (int b = 0; b < TB; b += 4)
+              *reinterpret_cast<float4 *>(d + b) = make_float4(acc[a][b], acc[a][b + 1], acc[a][b + 2], acc[a][b + 3]);
+          }
+        }
+#pragma unroll
+        for (int a = 0; a < TA; ++a)
+#pragma unroll
+          for (int b = 0; b < TB; ++b) acc[a][b] = 0.f;
+      }
+    }
+    __syncwarp();
+    kb = ts.kb_next;
+    zb = zbn;
+    ze = zen;
+    im = imn;
   }
 }
 
@@ -865,16 +1046,46 @@ __global__ void __launch_bounds__(kTtmcWarps * 32) ttmc_generic_kernel(const Ttm
   }
 }
 
-// Rows of slices split over several units: sum the partial rows in unit order.
-__global__ void ttmc_fixup_kernel(const uint32_t *long_k, const uint32_t *long_u0, const uint32_t *long_np,
-                                  const uint32_t *sid, const float *carry, float *Y, int64_t P) {
-  const int64_t l = blockIdx.x;
-  const uint32_t row = sid[long_k[l]], u0 = long_u0[l], np = long_np[l];
-  for (int64_t c = threadIdx.x; c < P; c += blockDim.x) {
-    float s = 0.f;
-    for (uint32_t q = 0; q < np; ++q) s += carry[(size_t)(u0 + q) * P + c];
-    Y[(size_t)row * P + c] = s;
+// Rows of slices split over several units: block (l, c) sums the partial rows of long
+// slice l for columns [32c, 32c + 32).  Warp w adds the pieces w, w + 8, ... (four loads in
+// flight), then the eight warp sums are added in warp order: a fixed order, so Y is
+// reproducible, and a slice cut into thousands of pieces is summed by many blocks.
+constexpr int kFixWarps = 8;
+__global__ void __launch_bounds__(kFixWarps * 32) ttmc_fixup_kernel(const uint32_t *long_k, const uint32_t *long_u0,
+                                                                     const uint32_t *long_np, const uint32_t *sid,
+                                                                     const float *carry, float *Y, int64_t P) {
+  __shared__ float part[kFixWarps][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t l = blockIdx.x, c = (int64_t)blockIdx.y * 32 + lane;
+  const uint32_t row = __ldg(sid + __ldg(long_k + l)), u0 = __ldg(long_u0 + l), np = __ldg(long_np + l);
+  float s = 0.f;
+  if (c < P) {
+    const float *base = carry + (size_t)u0 * P + c;
+    uint32_t q = (uint32_t)warp;
+    for (; q + 3u * kFixWarps < np; q += 4u * kFixWarps) {
+      float v[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v[k] = __ldcg(base + (size_t)(q + k * kFixWarps) * P);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) s += v[k];
+    }
+    for (; q < np; q += kFixWarps) s += __ldcg(base + (size_t)q * P);
   }
+  part[warp][lane] = s;
+  __syncthreads();
+  if (warp == 0 && c < P) {
+    float t = part[0][lane];
+#pragma unroll
+    for (int k = 1; k < kFixWarps; ++k) t += part[k][lane];
+    Y[(size_t)row * P + c] = t;
+  }
+}
+
+static void launch_fixup(const uint32_t *long_k, const uint32_t *long_u0, const uint32_t *long_np, int64_t n_long,
+                         const uint32_t *sid, const float *carry, float *Y, int64_t P, cudaStream_t s) {
+  const dim3 grid((unsigned)n_long, (unsigned)((P + 31) / 32));
+  ttmc_fixup_kernel<<<grid, kFixWarps * 32, 0, s>>>(long_k, long_u0, long_np, sid, carry, Y, P);
+  ::tk::count_launch();
 }
 
 __global__ void ttmc_zero_rows_kernel(const uint32_t *rows, int64_t n, float *Y, int64_t P) {
@@ -963,6 +1174,36 @@ static cudaError_t run_pipe(const TtmcParams &p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <int PL, int RB, int TA, int TB>
+static cudaError_t run_fiber(const TtmcParams &p, cudaStream_t s) {
+  const size_t smem = (size_t)kTtmcWarps * 32 * (PL + RB) * sizeof(float);
+  auto kern = ttmc_fiber_kernel<PL, RB, TA, TB>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const unsigned blocks = (unsigned)((p.n_units + kTtmcWarps - 1) / kTtmcWarps);
+  kern<<<blocks, kTtmcWarps * 32, smem, s>>>(p);
+  ::tk::count_launch();
+  return cudaGetLastError();
+}
+
+// Fiber-form FP32 dispatch (order 3, row-aligned factors).
+static bool dispatch_fiber(const TtmcParams &p, cudaStream_t s, cudaError_t *err) {
+  if (p.nother != 2) return false;
+  const int PL = p.R[0], RB = p.R[1];
+#define TK_FIB(PL_, RB_, TA_, TB_)                    \
+  {                                                   \
+    *err = run_fiber<PL_, RB_, TA_, TB_>(p, s);       \
+    return true;                                      \
+  }
+  if (PL == 16 && RB == 16) TK_FIB(16, 16, 4, 4)
+  if (PL == 8 && RB == 8) TK_FIB(8, 8, 2, 4)
+  if (PL == 32 && RB == 32) TK_FIB(32, 32, 8, 4)
+  if (PL == 16 && RB == 8) TK_FIB(16, 8, 4, 4)
+  if (PL == 8 && RB == 16) TK_FIB(8, 16, 4, 4)
+#undef TK_FIB
+  return false;
+}
+
 // Pipelined FP32 dispatch (order 3, row-aligned factors).
 static bool dispatch_pipe(const TtmcParams &p, cudaStream_t s, cudaError_t *err) {
   if (p.nother != 2) return false;
@@ -1049,6 +1290,33 @@ static tucker_status ttmc_impl(Ctx *c, int mode, float *Y, const float *val, con
   p.Y = Y;
   p.carry = c->carry;
   p.P = mc.P;
+  // FP32 factors with a fiber level: the fiber form, over fiber units
+  if (!bf16 && !(c->flags & (TUCKER_F_TF32X3 | TUCKER_F_UNPIPELINED)) && mc.fib && mc.fn_units > 0) {
+    TtmcParams q = p;
+    q.sptr = mc.fsptr;
+    q.unit_e0 = mc.funit_e0;
+    q.unit_k0 = mc.funit_k0;
+    q.unit_slot = mc.funit_slot;
+    q.n_units = mc.fn_units;
+    q.Z = (uint32_t)mc.F;
+    q.fptr = mc.fptr;
+    q.fmid = mc.fmid;
+    cudaError_t err = cudaSuccess;
+    if (dispatch_fiber(q, s, &err)) {
+      TK_CUDA(err);
+      if (mc.fn_long > 0) {
+        launch_fixup(mc.flong_k, mc.flong_u0, mc.flong_np, mc.fn_long, mc.sid, c->carry, Y, mc.P, s);
+        TK_CUDA(cudaGetLastError());
+      }
+      if (mc.n_empty > 0) {
+        ttmc_zero_rows_kernel<<<(unsigned)std::min<int64_t>(mc.n_empty, 65535), 256, 0, s>>>(mc.empty, mc.n_empty,
+                                                                                            Y, mc.P);
+        ::tk::count_launch();
+        TK_CUDA(cudaGetLastError());
+      }
+      return TUCKER_OK;
+    }
+  }
   if (mc.n_units > 0) {
     cudaError_t err = cudaSuccess;
     bool done = false;
@@ -1063,9 +1331,7 @@ static tucker_status ttmc_impl(Ctx *c, int mode, float *Y, const float *val, con
     TK_CUDA(err);
   }
   if (mc.n_long > 0) {
-    ttmc_fixup_kernel<<<(unsigned)mc.n_long, 256, 0, s>>>(mc.long_k, mc.long_u0, mc.long_np, mc.sid, c->carry, Y,
-                                                          mc.P);
-    ::tk::count_launch();
+    launch_fixup(mc.long_k, mc.long_u0, mc.long_np, mc.n_long, mc.sid, c->carry, Y, mc.P, s);
     TK_CUDA(cudaGetLastError());
   }
   if (mc.n_empty > 0) {
