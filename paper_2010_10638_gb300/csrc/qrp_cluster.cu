@@ -155,17 +155,39 @@ __device__ bool leaders_barrier(const CArgs &a, unsigned target) {
   return *(volatile unsigned *)(a.bar + 2) == 0u;
 }
 
-// sum over the S blocks of the cluster of entry q of their vectors `mine` (shared
-// memory), in rank order; all S loads are issued before the additions
+// Pairwise sum of 16 values in a fixed tree ((x0 + x1) + (x2 + x3)) + ...: depth 4
+// instead of a 15-long chain of dependent FP64 additions.
+__device__ __forceinline__ double tree16(double (&x)[16]) {
+#pragma unroll
+  for (int w = 1; w < 16; w <<= 1)
+#pragma unroll
+    for (int i = 0; i < 16; i += 2 * w) x[i] += x[i + w];
+  return x[0];
+}
+
+template <int NS>
+__device__ __forceinline__ double peer_tree(cg::cluster_group &cl, double *mine, int q) {
+  double x[NS];
+#pragma unroll
+  for (int r = 0; r < NS; ++r) x[r] = cl.map_shared_rank(mine, (unsigned)r)[q];
+#pragma unroll
+  for (int w = 1; w < NS; w <<= 1)
+#pragma unroll
+    for (int i = 0; i < NS; i += 2 * w) x[i] += x[i + w];
+  return x[0];
+}
+
+// sum over the S blocks of the cluster (S a power of two, at most 16) of entry q of
+// their vectors `mine` (shared memory), in a fixed tree over the ranks; all S loads are
+// issued before the additions
 __device__ __forceinline__ double peer_sum(cg::cluster_group &cl, double *mine, unsigned S, int q) {
-  double x[16];
-#pragma unroll
-  for (unsigned r = 0; r < 16; ++r) x[r] = (r < S) ? cl.map_shared_rank(mine, r)[q] : 0.0;
-  double t = x[0];
-#pragma unroll
-  for (unsigned r = 1; r < 16; ++r)
-    if (r < S) t += x[r];
-  return t;
+  switch (S) {
+    case 16: return peer_tree<16>(cl, mine, q);
+    case 8: return peer_tree<8>(cl, mine, q);
+    case 4: return peer_tree<4>(cl, mine, q);
+    case 2: return peer_tree<2>(cl, mine, q);
+    default: return mine[q];
+  }
 }
 
 struct Team {
@@ -176,10 +198,10 @@ struct Team {
 
 // Sums of the blocks' partial vectors `mine` (L doubles each, shared memory), in the
 // same order in every block: entries of this block's columns into svo, the scalar
-// entries n .. L-1 into svs.  False when a wait timed out (then no block reads a
-// peer's memory any more).
+// entries n .. L-1 into svs.  `scratch` holds ceil(clusters / 16) x (entries needed)
+// doubles.  False when a wait timed out (then no block reads a peer's memory any more).
 __device__ bool allreduce(const CArgs &a, cg::cluster_group &cl, Team &tm, double *mine, double *svo, double *svs,
-                          int par, int *s_ok) {
+                          int par, int *s_ok, double *scratch) {
   const int L = a.L, n = (int)a.n, ns = 2 * a.k + 2, need = tm.nown + ns;
   auto entry = [&](int t) { return t < tm.nown ? (int)tm.rank + (int)tm.S * t : n + (t - tm.nown); };
   auto store = [&](int t, double v) {
@@ -213,18 +235,25 @@ __device__ bool allreduce(const CArgs &a, cg::cluster_group &cl, Team &tm, doubl
     cl.sync();  // nobody reads rank 0's flag once it may have left
     return false;
   }
+  // the cluster sums this block needs: thread (entry t, chunk h) adds the clusters
+  // 16h .. 16h+15 of entry t in a fixed tree (one round trip for all of them), then the
+  // chunk sums of each entry are added in chunk order
   const double *base = a.slots + (size_t)par * a.nclusters * L;
-  for (int t = threadIdx.x; t < need; t += kCT) {
-    const int q = entry(t);
-    double sum = 0.0;
-    for (int c0 = 0; c0 < a.nclusters; c0 += 16) {  // 16 loads in flight, added in cluster order
-      double x[16];
+  const int nch = (a.nclusters + 15) / 16;
+  for (int idx = threadIdx.x; idx < need * nch; idx += kCT) {
+    const int t = idx % need, h = idx / need, q = entry(t);
+    double x[16];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) x[u] = (c0 + u < a.nclusters) ? __ldcg(base + (size_t)(c0 + u) * L + q) : 0.0;
-#pragma unroll
-      for (int u = 0; u < 16; ++u)
-        if (c0 + u < a.nclusters) sum += x[u];
+    for (int u = 0; u < 16; ++u) {
+      const int cc = 16 * h + u;
+      x[u] = (cc < a.nclusters) ? __ldcg(base + (size_t)cc * L + q) : 0.0;
     }
+    scratch[idx] = tree16(x);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < need; t += kCT) {
+    double sum = scratch[t];
+    for (int h = 1; h < nch; ++h) sum += scratch[h * need + t];
     store(t, sum);
   }
   __syncthreads();
@@ -541,7 +570,7 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
     ccolsum<AT, true>(a, As, ncache, r0, 0, nrows, ys, red4, rp);
     for (int q = (int)n + tid; q < L; q += kCT) rp[q] = 0.0;
     __syncthreads();
-    if (!allreduce(a, cl, tm, rp, svo, svs, par, &s_ok)) return cbail(a);
+    if (!allreduce(a, cl, tm, rp, svo, svs, par, &s_ok, red4)) return cbail(a);
     par ^= 1;
     for (int lc = tid; lc < tm.nown; lc += kCT) {
       vno[lc] = svo[lc];
@@ -600,10 +629,12 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
       if (g == 0) red4[kCT + warp * 32 + l] = u;  // [0, kCT) holds the ||y||^2 partials
     }
     __syncthreads();
-    if (warp == 0) {  // ||y||^2 partial: 16 per lane in order, then the lanes
-      double t = 0.0;
+    if (warp == 0) {  // ||y||^2 partial: a tree over each lane's 16 entries (lane + 32 q: no bank
+                      // conflicts), then over the lanes
+      double x[16];
 #pragma unroll
-      for (int q = 0; q < kCW; ++q) t += red4[lane * kCW + q];
+      for (int q = 0; q < kCW; ++q) x[q] = red4[q * 32 + lane];
+      double t = tree16(x);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
       if (lane == 0) {
@@ -611,19 +642,25 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
         rp[n + k + 1] = owner ? Vs[(j - r0) * kp + j] : 0.0;
       }
     }
-    for (int q = tid - 32; q >= 0 && q < k; q += kCT) {  // warps 1..: V^T y and row j of V
+    for (int q = tid - 32; q >= 0 && q < k; q += kCT) {  // warps 1..: V^T y (a tree over the warps), row j of V
       double t = 0.0;
-      if (q < j)
-        for (int w = 0; w < kCW; ++w) t += red4[kCT + w * 32 + q];
+      if (q < j) {
+        double x[16];
+#pragma unroll
+        for (int w = 0; w < kCW; ++w) x[w] = red4[kCT + w * 32 + q];
+        t = tree16(x);
+      }
       rp[n + q] = t;
       rp[n + k + 2 + q] = (owner && q < j) ? Vs[(j - r0) * kp + q] : 0.0;
     }
     // A^T y over this block's rows from row j on (its first barrier orders the above)
     ccolsum<AT, false>(a, As, ncache, r0, max((int64_t)0, (int64_t)j - r0), nrows, ys, red4, rp);
-    if (!allreduce(a, cl, tm, rp, svo, svs, par, &s_ok)) return cbail(a);
+    if (!allreduce(a, cl, tm, rp, svo, svs, par, &s_ok, red4)) return cbail(a);
     par ^= 1;
 
-    // ---- reflector (one thread), then F[:, j], row j of R, norm downdates
+    // ---- reflector (thread 0) while the column threads form the dot products that do not
+    //      depend on it: with u_l = s_l + V[j, l] v_jj (s_l = sum below row j),
+    //      F[c, :j] u = F[c, :j] s + v_jj (F[c, :j] V[j, :j]^T)
     if (tid == 0) {
       const double x0 = svs[k + 1];
       const double alpha = sqrt(svs[k]);
@@ -644,6 +681,24 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
         if (a.piv) a.piv[j] = c0;
       }
     }
+    const int lc = tid - 64;  // warps 2..: this block's columns (at most kCT - 64 of them)
+    const bool colt = lc >= 0 && lc < tm.nown && !doneo[lc];
+    double cs0 = 0.0, cs1 = 0.0, cv0 = 0.0, cv1 = 0.0;
+    if (colt) {
+      int l = 0;
+      for (; l + 1 < j; l += 2) {  // two independent chains each
+        const double f0 = Fo[(int64_t)l * no + lc], f1 = Fo[(int64_t)(l + 1) * no + lc];
+        cs0 = fma(f0, svs[l], cs0);
+        cs1 = fma(f1, svs[l + 1], cs1);
+        cv0 = fma(svs[k + 2 + l], f0, cv0);
+        cv1 = fma(svs[k + 2 + l + 1], f1, cv1);
+      }
+      if (l < j) {
+        const double f0 = Fo[(int64_t)l * no + lc];
+        cs0 = fma(f0, svs[l], cs0);
+        cv0 = fma(svs[k + 2 + l], f0, cv0);
+      }
+    }
     __syncthreads();
     const double v0 = s_sc[0], tau = s_sc[1], dv = s_sc[2];
     if (tid < j) {
@@ -652,22 +707,22 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
       su[tid] = fma(vj, v0, svs[tid]);  // V[:, l]^T v_j = sum below row j + V[j, l] v_jj
     }
     __syncthreads();
-    if (tid < j) {  // T(0:j, j) = -tau T(0:j, 0:j) u
-      double t = 0.0;
-      for (int q = tid; q < j; ++q) t = fma(Ts[tid * k + q], su[q], t);
-      Ts[tid * k + j] = -tau * t;
+    if (tid < j) {  // T(0:j, j) = -tau T(0:j, 0:j) u (two chains)
+      double t0 = 0.0, t1 = 0.0;
+      int q = tid;
+      for (; q + 1 < j; q += 2) {
+        t0 = fma(Ts[tid * k + q], su[q], t0);
+        t1 = fma(Ts[tid * k + q + 1], su[q + 1], t1);
+      }
+      if (q < j) t0 = fma(Ts[tid * k + q], su[q], t0);
+      Ts[tid * k + j] = -tau * (t0 + t1);
     }
     if (tid == 0) Ts[j * k + j] = tau;
-    for (int lc = tid - 64; lc >= 0 && lc < tm.nown; lc += kCT - 64) {  // warps 2..: this block's columns
-      if (doneo[lc]) continue;
+    if (colt) {
       const double ajc = ajo[lc];
       const double w = fma(dv, ajc, svo[lc]);  // A^T v = A^T y + (v_jj - y_jj) A[j, :]
-      double corr = 0.0, rv = 0.0;
-      for (int l = 0; l < j; ++l) {
-        const double fl = Fo[(int64_t)l * no + lc];
-        corr = fma(fl, su[l], corr);
-        rv = fma(Vt[j * k + l], fl, rv);
-      }
+      const double rv = cv0 + cv1;             // F[c, :j] V[j, :j]^T
+      const double corr = fma(v0, rv, cs0 + cs1);
       const double f = tau * (w - corr);
       Fo[(int64_t)j * no + lc] = f;
       double r = ajc - rv;
@@ -709,7 +764,7 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
           if (warp == 0) {
             double u = 0.0;
 #pragma unroll
-            for (int w = 0; w < kCW; ++w) u += red4[lane * kCW + w];
+            for (int w = 0; w < kCW; ++w) u += red4[w * 32 + lane];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
             if (lane == 0) rq[c] = u;
@@ -717,7 +772,7 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
           __syncthreads();
         }
       }
-      if (!allreduce(a, cl, tm, rq, svo, svs, par, &s_ok)) return cbail(a);
+      if (!allreduce(a, cl, tm, rq, svo, svs, par, &s_ok, red4)) return cbail(a);
       par ^= 1;
       for (int lc = tid; lc < tm.nown; lc += kCT) {
         if (flago[lc]) {
@@ -830,9 +885,11 @@ bool qrp_cluster(const AT *A, int64_t m, int64_t n, int64_t lda, int k, double *
   int S = 0, C = 0;
   int64_t rows_per = 0, rows_cached = 0;
   auto need = [&](int s_, int64_t rp, int64_t rc) { return clayout(n, k, L, s_, rp, rc, es).total; };
+  // a block's columns are handled by threads 64 .. kCT-1, one column each
+  auto cols_fit = [&](int s_) { return (n + s_ - 1) / s_ <= (int64_t)(kCT - 64); };
   // one cluster holding all of A in shared memory: no grid-wide barrier
   for (int si = 0; si < 2 && !S; ++si) {
-    if (d->max_clusters[si] < 1) continue;
+    if (d->max_clusters[si] < 1 || !cols_fit(kSizes[si])) continue;
     const int64_t rp = (m + kSizes[si] - 1) / kSizes[si];
     if (need(kSizes[si], rp, rp) <= avail) {
       S = kSizes[si];
@@ -848,7 +905,7 @@ bool qrp_cluster(const AT *A, int64_t m, int64_t n, int64_t lda, int k, double *
     for (int si = 1; si < 4; ++si) gmax = std::max(gmax, kSizes[si] * d->max_clusters[si]);
     if (gmax < 2) return false;
     for (int si = 1; si < 4 && !S; ++si) {
-      if (10 * kSizes[si] * d->max_clusters[si] >= 9 * gmax) {
+      if (10 * kSizes[si] * d->max_clusters[si] >= 9 * gmax && cols_fit(kSizes[si])) {
         S = kSizes[si];
         C = d->max_clusters[si];
       }
@@ -861,6 +918,7 @@ bool qrp_cluster(const AT *A, int64_t m, int64_t n, int64_t lda, int k, double *
   }
   const size_t smem = need(S, rows_per, rows_cached);
   if (C > 1 && 2 * (size_t)C * L > w->part_elems) return false;  // the cluster sums live in `part`
+  if ((int64_t)((C + 15) / 16) * ((n + S - 1) / S + 2 * k + 2) > 2 * kCT) return false;  // chunk sums: scratch
 
   CArgs a{};
   a.A = A;
