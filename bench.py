@@ -423,13 +423,13 @@ def run_mine(args):
         qbytes.append((k_ + 1) * m_ * n_ * 4.0 + 2.0 * m_ * k_ * 8.0)
     q_ms = sum(phase_ms[2 * n + 1] for n in big) / len(big)
     q_bytes = sum(qbytes) / len(qbytes)
-    qrp_roof = {"kernel": f"qrp_persistent_kernel<float> on the {max(w.dims)} x {ctx.P(big[0])} unfoldings",
+    qrp_roof = {"kernel": f"qrp_cluster_kernel<float> on the {max(w.dims)} x {ctx.P(big[0])} unfoldings",
                 "bound": "hbm", "achieved": q_bytes / (q_ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
                 "frac": q_bytes / (q_ms * 1e-3) / 1e9 / hbm_peak,
-                "traffic": profile_traffic("qrp_persistent_50000x256"),
+                "traffic": profile_traffic("qrp_cluster_50000x256"),
                 "peak_source": hbm_src, "alg_bytes_per_launch": q_bytes, "avg_launch_ms": q_ms,
-                "note": "k+1 passes over Y from L2 (DRAM traffic is about one pass); bound by synchronisation "
-                        "and on-chip latency"}
+                "note": "k+1 passes over Y, part of it held in shared memory and the rest read from L2 (DRAM "
+                        "traffic is about one pass); bound by the per-reflector synchronisation and FP64 latency"}
     dominant = ttmc_roof if ttmc_total >= qrp_total else qrp_roof
 
     cpu = None

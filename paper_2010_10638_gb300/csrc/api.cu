@@ -62,6 +62,10 @@ static tucker_status check_err_word(Ctx *c, cudaStream_t s) {
       c->last_error = "a bounded device-side wait gave up";
       return TUCKER_ETIMEOUT;
     }
+    if (bits & kErrLaunch) {
+      c->last_error = "a kernel was launched in a shape other than the one it was planned for";
+      return TUCKER_ECUDA;
+    }
     c->last_error = "device-side input check failed";
     return TUCKER_EINVAL;
   }

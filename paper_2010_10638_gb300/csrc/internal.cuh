@@ -17,6 +17,7 @@ constexpr int kMaxOrder = 8;
 constexpr uint32_t kErrCoord = 1u;    // a coordinate >= its dimension
 constexpr uint32_t kErrValue = 2u;    // a non-finite value
 constexpr uint32_t kErrTimeout = 4u;  // a bounded device-side wait gave up
+constexpr uint32_t kErrLaunch = 8u;   // a kernel found its launch shape different from its plan
 
 // Per-mode sorted copy of the nonzeros (a CSF root level over the non-empty slices)
 // and the work-unit table of the TTMc kernel.

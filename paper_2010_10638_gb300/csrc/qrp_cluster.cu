@@ -52,6 +52,7 @@ struct CArgs {
   int k;
   int L;          // partial-vector length n + 2k + 2
   int nclusters;  // clusters in the launch
+  int cluster;    // blocks per cluster the shared-memory plan was made for
   int vec4;       // FP32 A read as float4 (n % 4 == 0, lda % 4 == 0, 16-byte aligned)
   int64_t rows_per;     // rows of A per block
   int64_t rows_cached;  // leading rows of each block's range kept in shared memory
@@ -507,6 +508,12 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
   tm.S = cl.num_blocks();
   tm.rank = cl.block_rank();
   tm.epoch = 0;
+  // The shared-memory carve-up below depends on the cluster shape: a launch whose shape
+  // differs from the plan (the same in every block) reports an error and touches nothing.
+  if ((int)tm.S != a.cluster || (int)gridDim.x != a.cluster * a.nclusters) {
+    if (threadIdx.x == 0) atomicOr(a.err, kErrLaunch);
+    return cbail(a);
+  }
   const int64_t n = a.n, m = a.m;
   const int k = a.k, L = a.L;
   const CLayout lay = clayout(n, k, L, (int)tm.S, a.rows_per, a.rows_cached, (int)sizeof(AT));
@@ -928,6 +935,7 @@ bool qrp_cluster(const AT *A, int64_t m, int64_t n, int64_t lda, int k, double *
   a.k = k;
   a.L = L;
   a.nclusters = C;
+  a.cluster = S;
   a.vec4 = (es == 4 && n % 4 == 0 && lda % 4 == 0 && (reinterpret_cast<uintptr_t>(A) % 16) == 0) ? 1 : 0;
   a.rows_per = rows_per;
   a.rows_cached = rows_cached;
