@@ -463,6 +463,96 @@ def run_mine(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- paper experiments
+def _gpu_sweeps(T, torch, inst, iters, profile=False):
+    """init + `iters` HOOI sweeps on the GPU; returns (init_s, per-sweep ms list, fits, ctx)."""
+    w = inst.workload
+    coords = torch.as_tensor(inst.coords.astype(np.int32)).cuda()
+    vals = torch.as_tensor(inst.vals).cuda()
+    U0 = [torch.as_tensor(u).cuda() for u in inst.U0]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx = T.tucker_init(w.dims, coords, vals, w.ranks, U0)
+    torch.cuda.synchronize()
+    init_s = time.perf_counter() - t0
+    if profile:
+        T.tucker_set_profiling(ctx, True)
+    ms, fits, phases = [], [], []
+    for _ in range(iters):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fits.append(T.hooi_iter(ctx))
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+        if profile:
+            phases.append(T.tucker_phase_times(ctx))
+    return init_s, ms, fits, ctx, phases
+
+
+def run_fig7(args):
+    """Section IV-C, Fig. 7: whole decompositions of 200^3 random tensors, ranks 16, over a
+    range of sparsities; GPU (init + sweeps) beside the FP64 oracle on the host."""
+    import torch
+    import oracle
+    from paper_2010_10638_gb300 import build as libbuild, synth, tucker as T
+    libbuild.build()
+    T.load()
+    oracle.build()
+    rows = []
+    for i in range(len(synth.FIG7_DENSITIES)):
+        inst = synth.make(synth.fig7_workload(i))
+        w = inst.workload
+        _gpu_sweeps(T, torch, inst, 2)  # warm-up (first-use set-up of the kernels)
+        init_s, ms, fits, ctx, _ = _gpu_sweeps(T, torch, inst, w.iters)
+        T.tucker_free(ctx)
+        t0 = time.perf_counter()
+        ref = oracle.hooi(w.dims, w.ranks, inst.coords, inst.vals.astype(np.float64), inst.U0, w.iters)
+        t_or = time.perf_counter() - t0
+        gpu_s = init_s + sum(ms) * 1e-3
+        rows.append({"sparsity": w.nnz / float(np.prod(w.dims)), "nnz": w.nnz, "sweeps": w.iters,
+                     "gpu_s": gpu_s, "gpu_init_s": init_s, "gpu_sweep_ms": float(np.median(ms)),
+                     "oracle_s": t_or, "oracle_cores": 1, "speedup_vs_oracle": t_or / gpu_s,
+                     "fit_gpu": fits[-1], "fit_oracle": float(ref.fits[-1])})
+    print(json.dumps({"experiment": "fig7 sparsity sweep", "dims": [200, 200, 200], "ranks": [16, 16, 16],
+                      "data": "synthetic, distinct uniform coordinates, U(0,1) values", "rows": rows}), flush=True)
+    return 0
+
+
+def run_table3(args):
+    """Table III: the dense core TTM, a 32 x 32 x I3 tensor times a 32 x I3 factor, as the
+    core step of one sweep on a fully listed 32 x 32 x I3 tensor (ranks 32); the core
+    phase is timed with CUDA events inside hooi_iter, beside the oracle's core on the
+    same Y_(3) and U_3."""
+    import torch
+    import oracle
+    from paper_2010_10638_gb300 import build as libbuild, synth, tucker as T
+    libbuild.build()
+    T.load()
+    oracle.build()
+    rows = []
+    for i in range(len(synth.TABLE3_I3)):
+        inst = synth.make(synth.table3_workload(i))
+        w = inst.workload
+        _, _, _, ctx, phases = _gpu_sweeps(T, torch, inst, 12, profile=True)
+        core_ms = float(np.median([p[-1] for p in phases[2:]]))
+        Y3 = T.ttmc_mode(ctx, 2).cpu().numpy().astype(np.float64)
+        U3 = T.tucker_get_factor(ctx, 2).cpu().numpy()
+        T.tucker_free(ctx)
+        reps = 20
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            oracle.core(Y3, U3, w.ranks)
+        t_or = (time.perf_counter() - t0) / reps
+        flops = 2.0 * 32 * 32 * w.dims[2] * 32
+        rows.append({"I3": w.dims[2], "core_fit_ms": core_ms, "gflops": flops / (core_ms * 1e-3) / 1e9,
+                     "oracle_ms": t_or * 1e3, "oracle_cores": 1})
+    print(json.dumps({"experiment": "table3 core TTM", "shape": "(32 x 32 x I3) x_3 (32 x I3)^T -> 32 x 32 x 32",
+                      "note": "core_fit_ms is the core step of hooi_iter (core tensor, its norm and the fit)",
+                      "rows": rows}), flush=True)
+    return 0
+
+
 def _stream(s):
     return int(s.cuda_stream)
 
@@ -479,7 +569,13 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-bf16", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--fig7", action="store_true", help="Fig. 7 sparsity sweep (200^3, ranks 16) instead")
+    ap.add_argument("--table3", action="store_true", help="Table III core TTM shapes instead")
     args = ap.parse_args()
+    if args.fig7:
+        return run_fig7(args)
+    if args.table3:
+        return run_table3(args)
     if args.warmup < 3 and args.impl == "mine":
         args.warmup = 3
     if args.impl == "reference":

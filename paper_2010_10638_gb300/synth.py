@@ -64,6 +64,28 @@ WORKLOADS = {
 }
 
 
+# Section IV-C, Fig. 7: 200 x 200 x 200 random tensors of varying sparsity, ranks 16 (the
+# figure's sparsity values are not printed; this grid spans 1e-4 .. 0.3).
+FIG7_DENSITIES = (1e-4, 1e-3, 1e-2, 3e-2, 1e-1, 3e-1)
+
+
+def fig7_workload(i: int) -> Workload:
+    d = FIG7_DENSITIES[i]
+    return Workload(f"fig7-200^3-d{d:g}", (200, 200, 200), int(round(d * 200 ** 3)), (16, 16, 16), 5, 1100 + i,
+                    ("distinct",), "uniform")
+
+
+# Table III: the dense tensor-times-matrix of the core step, a 32 x 32 x I3 tensor times a
+# 32 x I3 factor, I3 = 32 .. 256 (all entries listed as nonzeros, ranks 32).
+TABLE3_I3 = (32, 64, 128, 256)
+
+
+def table3_workload(i: int) -> Workload:
+    i3 = TABLE3_I3[i]
+    return Workload(f"table3-32x32x{i3}", (32, 32, i3), 32 * 32 * i3, (32, 32, 32), 1, 1200 + i, ("distinct",),
+                    "normal")
+
+
 def zipf_indices(rng, n: int, size: int, s: float) -> np.ndarray:
     """Draw `size` indices on [0, n) with P(i) ~ (i+1)^-s, then relabel by a seeded permutation."""
     w = (np.arange(1, n + 1, dtype=np.float64)) ** (-s)
