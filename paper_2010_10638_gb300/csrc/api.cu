@@ -7,6 +7,8 @@
 #include <cstring>
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.cuh"
 
 using tk::Ctx;
@@ -16,6 +18,18 @@ struct tucker_ctx {
 };
 
 namespace tk {
+
+// NVTX ranges on the host timeline (shown by Nsight tools; a few nanoseconds otherwise).
+struct Range {
+  explicit Range(const char *name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range &) = delete;
+  Range &operator=(const Range &) = delete;
+};
+static const char *const kTtmcRange[kMaxOrder] = {"ttmc mode 0", "ttmc mode 1", "ttmc mode 2", "ttmc mode 3",
+                                                  "ttmc mode 4", "ttmc mode 5", "ttmc mode 6", "ttmc mode 7"};
+static const char *const kQrpRange[kMaxOrder] = {"qrp mode 0", "qrp mode 1", "qrp mode 2", "qrp mode 3",
+                                                 "qrp mode 4", "qrp mode 5", "qrp mode 6", "qrp mode 7"};
 
 static std::atomic<uint64_t> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -197,13 +211,18 @@ static tucker_status hooi_impl(Ctx *c, double *fit_out, cudaStream_t s) {
       return TUCKER_ERANK;
     }
   }
+  Range sweep("hooi_iter");
   tucker_status st = mark(c, 0, s);
   if (st != TUCKER_OK) return st;
   for (int n = 0; n < N; ++n) {
     const ModeCopy &mc = c->mode[n];
-    st = launch_ttmc(c, n, c->Y, s);
+    {
+      Range r(kTtmcRange[n]);
+      st = launch_ttmc(c, n, c->Y, s);
+    }
     if (st == TUCKER_OK) st = mark(c, 2 * n + 1, s);
     if (st != TUCKER_OK) return st;
+    Range rq(kQrpRange[n]);
     const int k = c->ranks[n];
     const int ncols = qrp_n_cols(c, n);
     QrpWork w;
@@ -220,7 +239,10 @@ static tucker_status hooi_impl(Ctx *c, double *fit_out, cudaStream_t s) {
     st = mark(c, 2 * n + 2, s);
     if (st != TUCKER_OK) return st;
   }
-  launch_core(c, c->Y, c->U64[N - 1], c->G, s);
+  {
+    Range r("core + fit");
+    launch_core(c, c->Y, c->U64[N - 1], c->G, s);
+  }
   TK_CUDA(cudaGetLastError());
   st = mark(c, 2 * N + 1, s);
   if (st != TUCKER_OK) return st;
@@ -319,6 +341,7 @@ tucker_status tucker_init(tucker_ctx **out, int order, const int64_t *dims, int6
   c->flags = flags;
   c->nnz_in = nnz;
   tk::reset_alloc_counter();
+  tk::Range r("tucker_init");
   tucker_status st = tk::init_impl(c, coords, vals, U0, seed, static_cast<cudaStream_t>(stream));
   if (st != TUCKER_OK) {
     // keep the message for the caller through a temporary context? The context is
@@ -333,6 +356,7 @@ tucker_status tucker_init(tucker_ctx **out, int order, const int64_t *dims, int6
 tucker_status ttmc_mode(tucker_ctx *h, int mode, float *Y, void *stream) {
   if (!h || !Y || mode < 0 || mode >= h->c.N) return TUCKER_EINVAL;
   if (reinterpret_cast<uintptr_t>(Y) % 16) return TUCKER_EINVAL;
+  tk::Range r("ttmc_mode");
   return tk::launch_ttmc(&h->c, mode, Y, static_cast<cudaStream_t>(stream));
 }
 
@@ -394,6 +418,7 @@ tucker_status qrp_leading(const double *A, int64_t m, int64_t n, int64_t lda, in
   if (!A || !Q || !work) return TUCKER_EINVAL;
   if (reinterpret_cast<uintptr_t>(work) % 256) return TUCKER_EINVAL;
   if (work_bytes < qrp_leading_work_bytes(m, n, k)) return TUCKER_EINVAL;
+  tk::Range r("qrp_leading");
   int dev = 0, sms = 1;
   if (cudaGetDevice(&dev) != cudaSuccess) return TUCKER_ECUDA;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return TUCKER_ECUDA;
@@ -407,6 +432,7 @@ tucker_status tucker_loss_grad(tucker_ctx *h, const float *const *U, const float
   if (!h || !U || !G || !loss || !dU || !dG) return TUCKER_EINVAL;
   for (int m = 0; m < h->c.N; ++m)
     if (!U[m] || !dU[m]) return TUCKER_EINVAL;
+  tk::Range r("tucker_loss_grad");
   return tk::launch_loss_grad(&h->c, U, G, loss, dU, dG, static_cast<cudaStream_t>(stream));
 }
 
