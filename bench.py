@@ -405,7 +405,8 @@ def run_mine(args):
     ttmc_avg_ms = sum(ttmc_ms) / N
     ttmc_flops = sum(flops) / N
     ttmc_bytes = sum(bytes_alg) / N
-    ttmc_roof = {"kernel": "ttmc_pipe_kernel<16,16,4,4> (+ fixup), FP32 form", "bound": "alu",
+    ttmc_roof = {"kernel": "FP32 TTMc: ttmc_pipe_kernel<16,16,4,4> (+ fixup); modes whose fibers are at most 1/4 of "
+                           "the nonzeros run ttmc_fibsum_kernel<16> then the same kernel over fibers", "bound": "alu",
                  "achieved": ttmc_flops / (ttmc_avg_ms * 1e-3) / 1e12, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                  "frac": ttmc_flops / (ttmc_avg_ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
                  "traffic": profile_traffic("ttmc_fp32_skew-20M"),

@@ -145,6 +145,21 @@ static tucker_status init_impl(Ctx *c, const uint32_t *coords, const float *vals
   for (int n = 0; n < N; ++n) PR *= c->ranks[n];
   TK_CUDA(dev_alloc(c, &c->Y, (size_t)ymax));
   TK_CUDA(dev_alloc(c, &c->carry, (size_t)carry_max));
+  {  // fiber form: factor sums, and the index / unit-value streams of its update pass
+    int64_t fmax = 0, tmax = 0;
+    for (int n = 0; n < N; ++n)
+      if (c->mode[n].fib) {
+        fmax = std::max(fmax, c->mode[n].F);
+        tmax = std::max(tmax, c->mode[n].F * (int64_t)c->ranks[c->mode[n].other[c->mode[n].nother - 1]]);
+      }
+    if (fmax > 0) {
+      TK_CUDA(dev_alloc(c, &c->fib_T, (size_t)tmax));
+      TK_CUDA(dev_alloc(c, &c->fib_iota, (size_t)fmax));
+      TK_CUDA(dev_alloc(c, &c->fib_ones, (size_t)fmax));
+      fill_iota_ones(c->fib_iota, c->fib_ones, fmax, s);
+      TK_CUDA(cudaGetLastError());
+    }
+  }
   TK_CUDA(dev_alloc(c, &c->gram, (size_t)gram_max));
   TK_CUDA(dev_alloc(c, &c->G, (size_t)PR));
   TK_CUDA(dev_alloc(c, &c->core_part, core_part_elems(c->num_sms, c->mode[N - 1].P, c->ranks[N - 1])));

@@ -104,6 +104,9 @@ struct Ctx {
 
   float *Y = nullptr;          // TTMc output of the current mode (max I_n * P_n floats)
   float *carry = nullptr;      // partial rows of split slices (max n_units * P_n floats)
+  float *fib_T = nullptr;      // fiber form: factor sums of the fibers (max F * R_last floats)
+  uint32_t *fib_iota = nullptr;  // fiber form: 0, 1, ..., F-1 (max F)
+  float *fib_ones = nullptr;   // fiber form: 1.0f (max F)
   double *gram = nullptr;      // Y Y^T for fat unfoldings
   double *G = nullptr;         // core tensor of the last sweep
   double *fit_dev = nullptr;   // fit of the last sweep (device)
@@ -152,6 +155,8 @@ tucker_status build_sorted_copies(Ctx *c, const uint32_t *coords, const float *v
 
 // ---- K-b: TTMc (ttmc.cu)
 tucker_status launch_ttmc(Ctx *c, int mode, float *Y, cudaStream_t s);
+// 0, 1, ..., n-1 and n ones (the index and value streams of the fiber form's update pass)
+void fill_iota_ones(uint32_t *iota, float *ones, int64_t n, cudaStream_t s);
 // TTMc of mode `mode` with values `val` (in that mode's sorted order) and FP32 factors
 // Uf[m] (indexed by mode; Uf[mode] unused) instead of the context's own.
 tucker_status launch_ttmc_ex(Ctx *c, int mode, float *Y, const float *val, const float *const *Uf, cudaStream_t s);

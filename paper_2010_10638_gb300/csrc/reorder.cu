@@ -521,17 +521,17 @@ static tucker_status build_units(Ctx *c, int64_t S, const uint32_t *ptr, int chu
 }
 
 // Whether mode copies of order-3 tensors get a fiber level (TUCKER_TTMC_FIBERS): "1"
-// always, "auto" when the fibers are at most kFiberShare of the nonzeros, otherwise never.
-// Off by default: on the 20M-nonzero skewed workload the fiber form, although it does
-// 2-4x fewer multiply-adds, ran slower than the nonzero form in every mode (its tiles
-// chain more dependent loads, and the Zipf-skewed fiber lengths leave lanes idle).
+// always, "0" never, otherwise when the fibers are at most kFiberShare of the nonzeros.
+// The fiber form forms t_f once per nonzero and one rank-1 update per fiber, so it pays
+// when fibers are long on average; on the 20M-nonzero skewed workload it ran faster than
+// the nonzero form at 0.17 fibers per nonzero and slower at 0.42.
 static int fiber_policy() {
   const char *f = std::getenv("TUCKER_TTMC_FIBERS");
   if (f && std::strcmp(f, "1") == 0) return 1;
-  if (f && std::strcmp(f, "auto") == 0) return -1;
-  return 0;
+  if (f && std::strcmp(f, "0") == 0) return 0;
+  return -1;
 }
-constexpr double kFiberShare = 0.6;
+constexpr double kFiberShare = 0.25;
 
 tucker_status build_sorted_copies(Ctx *c, const uint32_t *coords_in, const float *vals_in, cudaStream_t s) {
   const int N = c->N;

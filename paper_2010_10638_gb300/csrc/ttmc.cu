@@ -19,6 +19,7 @@
 //      row that a second kernel sums in piece order).
 // No global atomics: every output element has one writer, so Y is bitwise reproducible.
 #include <algorithm>
+#include <cstdlib>
 
 #include "internal.cuh"
 
@@ -398,180 +399,174 @@ __global__ void __launch_bounds__(kTtmcWarps * 32) ttmc_pipe_kernel(const TtmcPa
 // ============================================================================ fiber form
 // Order 3 with a fiber level (Section III-C, CSF): within a slice, the nonzeros that
 // share the index i_a of the first remaining mode form a fiber f (cut every kFiberCap
-// nonzeros), and the fiber contributes U_a(i_a, :) t_f^T with
-//     t_f = sum over its nonzeros of x_z U_b(i_b(z), :),
+// nonzeros); the slice row is the sum over its fibers of U_a(i_a(f), :) (x) t_f with
+//     t_f = sum over the nonzeros of f of x_z U_b(i_b(z), :),
 // so the RB-term sum is formed once per nonzero and the PL x RB rank-1 update once per
-// fiber.  Work units, slice offsets and long-slice pieces count fibers.  Per tile of 32
-// fibers the warp
-//   1. forms t_f with QL = RB / 4 lanes per fiber (lane s of the group owns
-//      t_f[4s, 4s+4)); group q holds the fibers q, q + 32/QL, ... of the tile and walks
-//      them side by side, UN nonzeros of each per step, so every factor-row load is one
-//      contiguous row per group and QL * UN rows per lane are in flight;
-//   2. stages U_a(i_a, :) and t_f in shared memory and accumulates the slice segments
-//      exactly as the nonzero form does.
-// Fiber offsets and middle indices of tile t+1 are prefetched during tile t.
-template <int PL, int RB, int TA, int TB>
-__global__ void __launch_bounds__(kTtmcWarps * 32) ttmc_fiber_kernel(const TtmcParams p) {
-  constexpr int G = (PL / TA) * (RB / TB);
-  constexpr int NG = 32 / G;
-  constexpr int QL = RB / 4;   // lanes per fiber in step 1
-  constexpr int FP = 32 / QL;  // fibers per group pass
-  constexpr int UN = RB >= 32 ? 1 : 2;  // nonzeros of each fiber per step
-  static_assert(G * NG == 32, "group size must divide the warp");
-  static_assert(PL % 4 == 0 && RB % 4 == 0 && QL <= 32 && 32 % QL == 0, "16-byte row pieces");
-  extern __shared__ float4 smem_f4[];
+// fiber.  Two passes over fiber work units:
+//   1. ttmc_fibsum_kernel writes t_f for every fiber (below);
+//   2. the nonzero form's pipelined kernel runs over the fibers as if they were nonzeros,
+//      with index stream fmid (rows of U_a), value 1 and the t_f rows as its last-mode rows
+//      (an identity index into t), so slices, split slices and the fixup are shared.
+//
+// Pass 1: one warp per run of `fpw` fibers (any run of whole fibers will do: t_f does not
+// depend on slices), windows of 32 consecutive nonzeros.  Lane (p, q) owns the
+// column quad q (t_f[4q, 4q+4)) of the QL = RB/4 consecutive positions of block p; the QL
+// lanes of a block read one whole factor row per position (coalesced), values and indices
+// come by shuffle from the coalesced loads (lane = position).  Each lane adds its positions
+// in order, writing the fibers that start and end inside its block; the piece before its
+// first fiber start (lead) and after its last (trail) are joined across blocks by a shuffle
+// scan over the maps "A -> A + lead" (no start) and "A -> trail" (a start), in block order,
+// applied to the fiber left open by the previous window.  Fixed orders: t is reproducible.
+template <int RB>
+__global__ void __launch_bounds__(kTtmcWarps * 32) ttmc_fibsum_kernel(const TtmcParams p, float *__restrict__ T,
+                                                                     int64_t fpw) {
+  constexpr int QL = RB / 4;    // lanes (column quads) per position block
+  constexpr int PG = 32 / QL;   // position blocks per window
+  constexpr int PB = 32 / PG;   // positions per block (= QL)
+  static_assert(RB % 4 == 0 && 32 % QL == 0, "RB in {4, 8, 16, 32}");
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  float *xa = reinterpret_cast<float *>(smem_f4) + w * 32 * (PL + RB);
-  float *bb = xa + 32 * PL;
-  const int64_t u = (int64_t)blockIdx.x * kTtmcWarps + w;
-  if (u >= p.n_units) return;
-  const float *UA = static_cast<const float *>(p.U[0]);
+  const int64_t u = (int64_t)blockIdx.x * kTtmcWarps + w;  // this warp's fibers: [u fpw, u fpw + fpw)
+  if (u * fpw >= (int64_t)p.Z) return;
   const float *UB = static_cast<const float *>(p.U[1]);
   const uint32_t *idxB = p.idx[1];
-  const uint32_t f0 = __ldg(p.unit_e0 + u);
-  const uint32_t f_end = (u + 1 < p.n_units) ? __ldg(p.unit_e0 + u + 1) : p.Z;
-  const int slot = __ldg(p.unit_slot + u);
-  const int ntiles = (int)((f_end - f0 + 31u) / 32u);
-  const int g = lane / G, j = lane % G;
-  const int ra0 = (j / (RB / TB)) * TA, rb0 = (j % (RB / TB)) * TB;
-  const int fq = lane / QL, s = lane % QL;
-  float acc[TA][TB];
+  const uint32_t f0 = (uint32_t)(u * fpw);
+  const uint32_t f_end = (uint32_t)min((int64_t)p.Z, u * fpw + fpw);
+  const uint32_t z0 = __ldg(p.fptr + f0), z1 = __ldg(p.fptr + f_end);
+  const int q = lane % QL, pb = lane / QL, P0 = pb * PB;
+  float4 *T4 = reinterpret_cast<float4 *>(T);
+  uint32_t kb = f0;                           // fiber of the window's first nonzero
+  float4 carry = make_float4(0.f, 0.f, 0.f, 0.f);  // what fiber kb gathered in earlier windows
+  float x = 0.f;
+  uint32_t ib = 0u;
+  if (z0 + lane < z1) {
+    x = __ldg(p.val + z0 + lane);
+    ib = __ldg(idxB + z0 + lane);
+  }
+  uint32_t bound = (kb + 1u + lane <= p.Z) ? __ldg(p.fptr + kb + 1u + lane) : 0xffffffffu;
+  for (uint32_t z = z0; z < z1; z += 32u) {
+    const int nt = (int)min(32u, z1 - z);
+    const uint32_t qq = bound - z;
+    uint32_t starts = __reduce_or_sync(kFull, qq < 32u ? (1u << qq) : 0u);  // bit s: a fiber starts at s (s >= 1)
+    starts &= (nt >= 32) ? kFull : ((1u << nt) - 1u);
+    const bool end_is_start = __any_sync(kFull, qq == (uint32_t)nt);
+    const uint32_t kb_next = kb + __popc(__ballot_sync(kFull, qq <= (uint32_t)nt));
+    const uint32_t bound_next = (kb_next + 1u + lane <= p.Z) ? __ldg(p.fptr + kb_next + 1u + lane) : 0xffffffffu;
+    float xn = 0.f;
+    uint32_t ibn = 0u;
+    if (z + 32u + lane < z1) {
+      xn = __ldg(p.val + z + 32u + lane);
+      ibn = __ldg(idxB + z + 32u + lane);
+    }
+    auto fiber_of = [&](int s) { return kb + (uint32_t)__popc(starts & ((2u << s) - 1u)); };
+    // this block's rows: all loads first
+    float xv[PB];
+    float4 r[PB];
 #pragma unroll
-  for (int a = 0; a < TA; ++a)
+    for (int i = 0; i < PB; ++i) {
+      xv[i] = __shfl_sync(kFull, x, P0 + i);
+      const uint32_t rr = __shfl_sync(kFull, ib, P0 + i);
+      r[i] = (P0 + i < nt) ? __ldg(reinterpret_cast<const float4 *>(UB + (size_t)rr * RB) + q)
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    // local pass: lead piece, fibers inside the block, trail piece
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f), lead = acc;
+    bool seen = false;
 #pragma unroll
-    for (int b = 0; b < TB; ++b) acc[a][b] = 0.f;
+    for (int i = 0; i < PB; ++i) {
+      if ((starts >> (P0 + i)) & 1u) {  // the fiber at P0 + i - 1 ends
+        if (seen)
+          T4[(size_t)fiber_of(P0 + i - 1) * QL + q] = acc;
+        else
+          lead = acc;
+        seen = true;
+        acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      acc.x = fmaf(xv[i], r[i].x, acc.x);
+      acc.y = fmaf(xv[i], r[i].y, acc.y);
+      acc.z = fmaf(xv[i], r[i].z, acc.z);
+      acc.w = fmaf(xv[i], r[i].w, acc.w);
+    }
+    if (!seen) lead = acc;
+    // block map: A -> (seen ? 0 : A) + (seen ? trail : lead); inclusive scan over blocks
+    bool cz = seen;  // composed map resets A
+    float4 cb = seen ? acc : lead;
+#pragma unroll
+    for (int d = 1; d < PG; d <<= 1) {
+      const bool ez = __shfl_up_sync(kFull, (int)cz, d * QL) != 0;
+      float4 eb;
+      eb.x = __shfl_up_sync(kFull, cb.x, d * QL);
+      eb.y = __shfl_up_sync(kFull, cb.y, d * QL);
+      eb.z = __shfl_up_sync(kFull, cb.z, d * QL);
+      eb.w = __shfl_up_sync(kFull, cb.w, d * QL);
+      if (pb >= d && !cz) {  // (this, covering later blocks) after (earlier): keep earlier's reset, add
+        cz = ez;
+        cb.x = eb.x + cb.x;
+        cb.y = eb.y + cb.y;
+        cb.z = eb.z + cb.z;
+        cb.w = eb.w + cb.w;
+      }
+    }
+    // open fiber entering this block = (composition of blocks before it)(carry)
+    const bool pz = __shfl_up_sync(kFull, (int)cz, QL) != 0;
+    float4 pbv;
+    pbv.x = __shfl_up_sync(kFull, cb.x, QL);
+    pbv.y = __shfl_up_sync(kFull, cb.y, QL);
+    pbv.z = __shfl_up_sync(kFull, cb.z, QL);
+    pbv.w = __shfl_up_sync(kFull, cb.w, QL);
+    float4 open = carry;
+    if (pb > 0) {
+      if (pz) {
+        open = pbv;
+      } else {
+        open.x = carry.x + pbv.x;
+        open.y = carry.y + pbv.y;
+        open.z = carry.z + pbv.z;
+        open.w = carry.w + pbv.w;
+      }
+    }
+    if (seen) {  // the open fiber ends at this block's first start
+      const int s0 = __ffs(starts & (((PB + P0) >= 32 ? kFull : ((1u << (P0 + PB)) - 1u)) & ~((1u << P0) - 1u))) - 1;
+      T4[(size_t)fiber_of(s0 - 1) * QL + q] =
+          make_float4(open.x + lead.x, open.y + lead.y, open.z + lead.z, open.w + lead.w);
+    }
+    // the fiber open at the end of the window: the last block's composition applied to carry
+    const int last = PG - 1;
+    const bool lz = __shfl_sync(kFull, (int)cz, last * QL + q) != 0;
+    float4 fin;
+    fin.x = __shfl_sync(kFull, cb.x, last * QL + q);
+    fin.y = __shfl_sync(kFull, cb.y, last * QL + q);
+    fin.z = __shfl_sync(kFull, cb.z, last * QL + q);
+    fin.w = __shfl_sync(kFull, cb.w, last * QL + q);
+    if (!lz) {
+      fin.x = carry.x + fin.x;
+      fin.y = carry.y + fin.y;
+      fin.z = carry.z + fin.z;
+      fin.w = carry.w + fin.w;
+    }
+    if (end_is_start || z + (uint32_t)nt == z1) {
+      if (pb == 0) T4[(size_t)fiber_of(nt - 1) * QL + q] = fin;
+      carry = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+      carry = fin;
+    }
+    kb = kb_next;
+    bound = bound_next;
+    x = xn;
+    ib = ibn;
+  }
+}
 
-  uint32_t kb = __ldg(p.unit_k0 + u);
-  // fiber bounds and middle index of lane's fiber in tile 0 (later tiles: prefetched)
-  uint32_t zb = 0u, ze = 0u, im = 0u;
-  if (f0 + lane < f_end) {
-    zb = __ldg(p.fptr + f0 + lane);
-    ze = __ldg(p.fptr + f0 + lane + 1);
-    im = __ldg(p.fmid + f0 + lane);
+__global__ void fill_iota_ones_kernel(uint32_t *iota, float *ones, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    iota[i] = (uint32_t)i;
+    ones[i] = 1.0f;
   }
-  for (int t = 0; t < ntiles; ++t) {
-    const uint32_t e = f0 + 32u * (uint32_t)t;
-    const int nt = (int)min(32u, f_end - e);
-    const TileSlices ts = tile_slices(p.sptr, p.S, kb, e, nt, lane);
-    uint32_t zbn = 0u, zen = 0u, imn = 0u;
-    if (e + 32u + (uint32_t)lane < f_end) {
-      zbn = __ldg(p.fptr + e + 32u + lane);
-      zen = __ldg(p.fptr + e + 33u + lane);
-      imn = __ldg(p.fmid + e + 32u + lane);
-    }
-    // 1. t_f: this group's QL fibers side by side
-    uint32_t zc[QL], zn[QL];
-#pragma unroll
-    for (int k = 0; k < QL; ++k) {
-      const int fl = k * FP + fq;
-      const uint32_t b0 = __shfl_sync(kFull, zb, fl), b1 = __shfl_sync(kFull, ze, fl);
-      zc[k] = b0;
-      zn[k] = (fl < nt) ? b1 : b0;
-    }
-    float4 tq[QL];
-#pragma unroll
-    for (int k = 0; k < QL; ++k) tq[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-    bool more = false;
-#pragma unroll
-    for (int k = 0; k < QL; ++k) more |= zc[k] < zn[k];
-    while (__any_sync(kFull, more)) {
-      float xv[QL][UN];
-      uint32_t iv[QL][UN];
-#pragma unroll
-      for (int k = 0; k < QL; ++k)
-#pragma unroll
-        for (int v = 0; v < UN; ++v) {
-          const uint32_t z = zc[k] + (uint32_t)v;
-          const bool ok = z < zn[k];
-          xv[k][v] = ok ? __ldg(p.val + z) : 0.f;
-          iv[k][v] = ok ? __ldg(idxB + z) : 0xffffffffu;
-        }
-      float4 r[QL][UN];
-#pragma unroll
-      for (int k = 0; k < QL; ++k)
-#pragma unroll
-        for (int v = 0; v < UN; ++v)
-          r[k][v] = iv[k][v] != 0xffffffffu
-                        ? __ldg(reinterpret_cast<const float4 *>(UB + (size_t)iv[k][v] * RB) + s)
-                        : make_float4(0.f, 0.f, 0.f, 0.f);
-      more = false;
-#pragma unroll
-      for (int k = 0; k < QL; ++k) {
-#pragma unroll
-        for (int v = 0; v < UN; ++v) {
-          tq[k].x = fmaf(xv[k][v], r[k][v].x, tq[k].x);
-          tq[k].y = fmaf(xv[k][v], r[k][v].y, tq[k].y);
-          tq[k].z = fmaf(xv[k][v], r[k][v].z, tq[k].z);
-          tq[k].w = fmaf(xv[k][v], r[k][v].w, tq[k].w);
-        }
-        zc[k] += UN;
-        more |= zc[k] < zn[k];
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < QL; ++k)  // zero rows past the tile's fibers
-      *reinterpret_cast<float4 *>(bb + (k * FP + fq) * RB + 4 * s) = tq[k];
-    // 2. the middle rows U_a(i_a, :), then the slice segments
-#pragma unroll
-    for (int it = lane; it < 32 * (PL / 4); it += 32) {
-      const int tt = it / (PL / 4), c = (it % (PL / 4)) * 4;
-      const uint32_t r = __shfl_sync(kFull, im, tt);
-      if (tt < nt)
-        *reinterpret_cast<float4 *>(xa + tt * PL + c) = __ldg(reinterpret_cast<const float4 *>(UA + (size_t)r * PL + c));
-    }
-    __syncwarp();
-    // slice segments of the tile
-    uint32_t segs = ts.starts | 1u;
-    while (segs) {
-      const int p0 = __ffs(segs) - 1;
-      segs &= segs - 1u;
-      const int p1 = segs ? (__ffs(segs) - 1) : nt;
-      int qq = p0 + g;
-      auto step = [&](int r) {
-        float av[TA], bv[TB];
-        lds<TA>(xa + r * PL + ra0, av);
-        lds<TB>(bb + r * RB + rb0, bv);
-#pragma unroll
-        for (int a = 0; a < TA; ++a)
-#pragma unroll
-          for (int b = 0; b < TB; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
-      };
-      for (; qq + NG < p1; qq += 2 * NG) {
-        step(qq);
-        step(qq + NG);
-      }
-      if (qq < p1) step(qq);
-      const bool flush = (p1 < nt) || ts.end_is_start || (e + (uint32_t)nt == f_end);
-      if (flush) {
-#pragma unroll
-        for (int o = G; o < 32; o <<= 1)
-#pragma unroll
-          for (int a = 0; a < TA; ++a)
-#pragma unroll
-            for (int b = 0; b < TB; ++b) acc[a][b] += __shfl_xor_sync(kFull, acc[a][b], o);
-        const uint32_t kseg = __shfl_sync(kFull, ts.kp, p0);
-        if (g == 0) {
-          float *dst = (slot >= 0) ? p.carry + (size_t)slot * p.P : p.Y + (size_t)__ldg(p.sid + kseg) * p.P;
-#pragma unroll
-          for (int a = 0; a < TA; ++a) {
-            float *d = dst + (size_t)(ra0 + a) * RB + rb0;
-#pragma unroll
-            for (int b = 0; b < TB; b += 4)
-              *reinterpret_cast<float4 *>(d + b) = make_float4(acc[a][b], acc[a][b + 1], acc[a][b + 2], acc[a][b + 3]);
-          }
-        }
-#pragma unroll
-        for (int a = 0; a < TA; ++a)
-#pragma unroll
-          for (int b = 0; b < TB; ++b) acc[a][b] = 0.f;
-      }
-    }
-    __syncwarp();
-    kb = ts.kb_next;
-    zb = zbn;
-    ze = zen;
-    im = imn;
-  }
+}
+
+void fill_iota_ones(uint32_t *iota, float *ones, int64_t n, cudaStream_t s) {
+  const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 65535));
+  fill_iota_ones_kernel<<<blocks, 256, 0, s>>>(iota, ones, n);
+  ::tk::count_launch();
 }
 
 // ============================================================================ tensor-core form
@@ -1174,34 +1169,38 @@ static cudaError_t run_pipe(const TtmcParams &p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int PL, int RB, int TA, int TB>
-static cudaError_t run_fiber(const TtmcParams &p, cudaStream_t s) {
-  const size_t smem = (size_t)kTtmcWarps * 32 * (PL + RB) * sizeof(float);
-  auto kern = ttmc_fiber_kernel<PL, RB, TA, TB>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  const unsigned blocks = (unsigned)((p.n_units + kTtmcWarps - 1) / kTtmcWarps);
-  kern<<<blocks, kTtmcWarps * 32, smem, s>>>(p);
+template <int RB>
+static cudaError_t run_fibsum(const TtmcParams &p, float *T, int64_t nnz, cudaStream_t s) {
+  // 64 fibers per warp (measured best on the skewed 20M-nonzero workload; many short warps
+  // balance the Zipf-skewed fiber lengths)
+  const int64_t F = std::max<int64_t>(p.Z, 1);
+  (void)nnz;
+  int64_t fpw = 64;
+  if (const char *e = std::getenv("TUCKER_FIBSUM_FPW")) fpw = std::max<int64_t>(32, std::atoll(e) / 32 * 32);
+  const int64_t warps = (F + fpw - 1) / fpw;
+  const unsigned blocks = (unsigned)((warps + kTtmcWarps - 1) / kTtmcWarps);
+  ttmc_fibsum_kernel<RB><<<blocks, kTtmcWarps * 32, 0, s>>>(p, T, fpw);
   ::tk::count_launch();
   return cudaGetLastError();
 }
 
-// Fiber-form FP32 dispatch (order 3, row-aligned factors).
-static bool dispatch_fiber(const TtmcParams &p, cudaStream_t s, cudaError_t *err) {
+// Fiber sums for the shapes the update pass covers (order 3, RB in {8, 16, 32}).
+static bool dispatch_fibsum(const TtmcParams &p, float *T, int64_t nnz, cudaStream_t s, cudaError_t *err) {
   if (p.nother != 2) return false;
-  const int PL = p.R[0], RB = p.R[1];
-#define TK_FIB(PL_, RB_, TA_, TB_)                    \
-  {                                                   \
-    *err = run_fiber<PL_, RB_, TA_, TB_>(p, s);       \
-    return true;                                      \
-  }
-  if (PL == 16 && RB == 16) TK_FIB(16, 16, 4, 4)
-  if (PL == 8 && RB == 8) TK_FIB(8, 8, 2, 4)
-  if (PL == 32 && RB == 32) TK_FIB(32, 32, 8, 4)
-  if (PL == 16 && RB == 8) TK_FIB(16, 8, 4, 4)
-  if (PL == 8 && RB == 16) TK_FIB(8, 16, 4, 4)
-#undef TK_FIB
-  return false;
+  const int RB = p.R[1];
+  if (RB == 16) *err = run_fibsum<16>(p, T, nnz, s);
+  else if (RB == 8) *err = run_fibsum<8>(p, T, nnz, s);
+  else if (RB == 32) *err = run_fibsum<32>(p, T, nnz, s);
+  else return false;
+  return true;
+}
+
+static bool dispatch_pipe(const TtmcParams &p, cudaStream_t s, cudaError_t *err);
+
+// shapes (first rank, last rank) of the pipelined kernel below
+static bool pipe_shape(int PL, int RB) {
+  return (PL == 16 && RB == 16) || (PL == 8 && RB == 8) || (PL == 32 && RB == 32) || (PL == 16 && RB == 8) ||
+         (PL == 8 && RB == 16);
 }
 
 // Pipelined FP32 dispatch (order 3, row-aligned factors).
@@ -1290,8 +1289,9 @@ static tucker_status ttmc_impl(Ctx *c, int mode, float *Y, const float *val, con
   p.Y = Y;
   p.carry = c->carry;
   p.P = mc.P;
-  // FP32 factors with a fiber level: the fiber form, over fiber units
-  if (!bf16 && !(c->flags & (TUCKER_F_TF32X3 | TUCKER_F_UNPIPELINED)) && mc.fib && mc.fn_units > 0) {
+  // FP32 factors with a fiber level: fiber sums, then the pipelined update over fibers
+  if (!bf16 && !(c->flags & (TUCKER_F_TF32X3 | TUCKER_F_UNPIPELINED)) && mc.fib && mc.fn_units > 0 && c->fib_T &&
+      p.nother == 2 && pipe_shape(p.R[0], p.R[1])) {
     TtmcParams q = p;
     q.sptr = mc.fsptr;
     q.unit_e0 = mc.funit_e0;
@@ -1302,18 +1302,22 @@ static tucker_status ttmc_impl(Ctx *c, int mode, float *Y, const float *val, con
     q.fptr = mc.fptr;
     q.fmid = mc.fmid;
     cudaError_t err = cudaSuccess;
-    if (dispatch_fiber(q, s, &err)) {
+    if (dispatch_fibsum(q, c->fib_T, c->nnz, s, &err)) {
       TK_CUDA(err);
-      if (mc.fn_long > 0) {
-        launch_fixup(mc.flong_k, mc.flong_u0, mc.flong_np, mc.fn_long, mc.sid, c->carry, Y, mc.P, s);
-        TK_CUDA(cudaGetLastError());
-      }
+      TtmcParams r = q;  // the fibers as nonzeros: rows U_a(fmid[f]) and t_f, value 1
+      r.idx[0] = mc.fmid;
+      r.idx[1] = c->fib_iota;
+      r.U[1] = c->fib_T;
+      r.val = c->fib_ones;
+      dispatch_pipe(r, s, &err);  // covers the shape (checked above)
+      TK_CUDA(err);
+      if (mc.fn_long > 0) launch_fixup(mc.flong_k, mc.flong_u0, mc.flong_np, mc.fn_long, mc.sid, c->carry, Y, mc.P, s);
       if (mc.n_empty > 0) {
         ttmc_zero_rows_kernel<<<(unsigned)std::min<int64_t>(mc.n_empty, 65535), 256, 0, s>>>(mc.empty, mc.n_empty,
                                                                                             Y, mc.P);
         ::tk::count_launch();
-        TK_CUDA(cudaGetLastError());
       }
+      TK_CUDA(cudaGetLastError());
       return TUCKER_OK;
     }
   }
