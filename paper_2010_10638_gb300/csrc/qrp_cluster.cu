@@ -45,6 +45,19 @@ namespace {
 constexpr int kCT = 512;  // threads per block, one block per SM
 constexpr int kCW = kCT / 32;
 constexpr unsigned long long kCSpin = 1ull << 25;  // polls before a barrier wait gives up
+// During a reflector step the first kColT threads form A^T y (FP32 pipe) while the last
+// kCT - kColT threads form V^T y and ||y||^2 (FP64 pipe), each group with its own barrier.
+constexpr int kColT = 448;
+constexpr int kAuxT = kCT - kColT;
+
+// barrier of the first NT threads of the block (all of them: __syncthreads)
+template <int NT>
+__device__ __forceinline__ void group_sync() {
+  if constexpr (NT == kCT)
+    __syncthreads();
+  else
+    asm volatile("bar.sync 1, %0;\n" ::"r"(NT) : "memory");
+}
 
 struct CArgs {
   const void *A;
@@ -67,7 +80,8 @@ struct CArgs {
 
 // Dynamic shared memory of one block; the same arithmetic on host and device.
 struct CLayout {
-  size_t Fo, vno, vrefo, ajo, svo, svs, flago, doneo, red, Ts, Vt, Ms, su, Vs, red4, ys, perm, posof, cand, As, total;
+  size_t Fo, vno, vrefo, ajo, svo, svs, flago, doneo, red, Ts, Vt, Ms, su, Vs, red4, cscr, ys, perm, posof, cand, As,
+      total;
   int kp;      // row stride of Vs in doubles (odd: rows fall in different banks)
   int64_t no;  // columns per block, rounded up
 };
@@ -96,6 +110,7 @@ __host__ __device__ inline CLayout clayout(int64_t n, int k, int L, int S, int64
   l.su = o;    o += c16(sizeof(double) * 64);
   l.Vs = o;    o += c16(sizeof(double) * (size_t)rows_per * l.kp);  // this block's rows of V
   l.red4 = o;  o += c16(sizeof(double) * 2 * kCT);        // reduction scratch (8 KB)
+  l.cscr = o;  o += c16(sizeof(double) * 2 * kCT);        // column-sum scratch (8 KB)
   l.ys = o;    o += c16(sizeof(double) * (size_t)rows_per);  // y per row (float2 or double)
   l.perm = o;  o += c16(sizeof(int) * (size_t)n);
   l.posof = o; o += c16(sizeof(int) * (size_t)n);
@@ -316,8 +331,8 @@ __device__ __forceinline__ DF df_of(float2 p) {
 
 // out[c], c < n: sum over local rows li in [l0, nrows) of A[r0 + li, c] * y_li (SQUARE:
 // A[r0 + li, c]^2).  Rows li < ncache come from the shared copy As (row stride n).
-// `scratch` holds 2 * kCT doubles.
-template <typename AT, bool SQUARE>
+// Run by the first NT threads (NT a multiple of 32); `scratch` holds 2 * NT doubles.
+template <typename AT, bool SQUARE, int NT>
 __device__ void ccolsum(const CArgs &a, const AT *As, int64_t ncache, int64_t r0, int64_t l0, int64_t nrows,
                         const void *ys, void *scratch, double *out) {
   const int64_t n = a.n;
@@ -329,12 +344,13 @@ __device__ void ccolsum(const CArgs &a, const AT *As, int64_t ncache, int64_t r0
     if (a.vec4) {
       const int64_t nq = n / 4, ld4 = a.lda / 4, sn4 = n / 4;
       int cw = 8;
-      while (cw < nq && cw < kCT) cw <<= 1;
-      const int nrl = kCT / cw, cq = threadIdx.x % cw, rl = threadIdx.x / cw;
+      while (cw < nq && cw * 2 <= NT) cw <<= 1;  // cw <= NT
+      const int nrl = NT / cw, cq = threadIdx.x % cw, rl = threadIdx.x / cw;
+      const bool act = rl < nrl;  // NT need not be a multiple of cw
       for (int64_t q0 = 0; q0 < nq; q0 += cw) {
         const int64_t qc = q0 + cq;
         DF d[4];
-        if (qc < nq) {
+        if (act && qc < nq) {
           seg4<false, SQUARE>(reinterpret_cast<const float4 *>(As) + qc, sn4, l0, min(nrows, ncache), rl, nrl, y2,
                               d[0], d[1], d[2], d[3]);
           seg4<true, SQUARE>(reinterpret_cast<const float4 *>(A) + r0 * ld4 + qc, ld4, max(l0, ncache), nrows, rl,
@@ -342,30 +358,31 @@ __device__ void ccolsum(const CArgs &a, const AT *As, int64_t ncache, int64_t r0
         }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {  // two columns of the four at a time through the scratch
-          __syncthreads();
+          group_sync<NT>();
           red[threadIdx.x] = make_float2(d[2 * h].hi, d[2 * h].lo);
-          red[kCT + threadIdx.x] = make_float2(d[2 * h + 1].hi, d[2 * h + 1].lo);
-          __syncthreads();
+          red[NT + threadIdx.x] = make_float2(d[2 * h + 1].hi, d[2 * h + 1].lo);
+          group_sync<NT>();
           if (rl == 0 && qc < nq) {
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
               DF t = d[2 * h + q];
-              for (int r = 1; r < nrl; ++r) df_add(t, df_of(red[q * kCT + r * cw + cq]));
+              for (int r = 1; r < nrl; ++r) df_add(t, df_of(red[q * NT + r * cw + cq]));
               out[4 * qc + 2 * h + q] = (double)t.hi + (double)t.lo;
             }
           }
         }
       }
-      __syncthreads();
+      group_sync<NT>();
       return;
     }
     int cw = 32;
-    while (cw < n && cw < kCT) cw <<= 1;
-    const int nrl = kCT / cw, cl = threadIdx.x % cw, rl = threadIdx.x / cw;
+    while (cw < n && cw * 2 <= NT) cw <<= 1;  // cw <= NT
+    const int nrl = NT / cw, cl = threadIdx.x % cw, rl = threadIdx.x / cw;
+    const bool act = rl < nrl;
     for (int64_t c0 = 0; c0 < n; c0 += cw) {
       const int64_t c = c0 + cl;
       DF d;
-      if (c < n) {
+      if (act && c < n) {
         for (int64_t li = l0 + rl; li < nrows; li += nrl) {
           const float x = li < ncache ? (float)As[li * n + c] : (float)__ldg(A + (r0 + li) * a.lda + c);
           if (SQUARE) {
@@ -376,41 +393,42 @@ __device__ void ccolsum(const CArgs &a, const AT *As, int64_t ncache, int64_t r0
           }
         }
       }
-      __syncthreads();
+      group_sync<NT>();
       red[threadIdx.x] = make_float2(d.hi, d.lo);
-      __syncthreads();
+      group_sync<NT>();
       if (rl == 0 && c < n) {
         DF t = d;
         for (int r = 1; r < nrl; ++r) df_add(t, df_of(red[r * cw + cl]));
         out[c] = (double)t.hi + (double)t.lo;
       }
     }
-    __syncthreads();
+    group_sync<NT>();
   } else {
     double *red = static_cast<double *>(scratch);
     const double *yd = static_cast<const double *>(ys);
     int cw = 32;
-    while (cw < n && cw < kCT) cw <<= 1;
-    const int nrl = kCT / cw, cl = threadIdx.x % cw, rl = threadIdx.x / cw;
+    while (cw < n && cw * 2 <= NT) cw <<= 1;  // cw <= NT
+    const int nrl = NT / cw, cl = threadIdx.x % cw, rl = threadIdx.x / cw;
+    const bool act = rl < nrl;
     for (int64_t c0 = 0; c0 < n; c0 += cw) {
       const int64_t c = c0 + cl;
       double acc = 0.0;
-      if (c < n) {
+      if (act && c < n) {
         for (int64_t li = l0 + rl; li < nrows; li += nrl) {
           const double x = li < ncache ? (double)As[li * n + c] : (double)__ldg(A + (r0 + li) * a.lda + c);
           acc = fma(x, SQUARE ? x : yd[li], acc);
         }
       }
-      __syncthreads();
+      group_sync<NT>();
       red[threadIdx.x] = acc;
-      __syncthreads();
+      group_sync<NT>();
       if (rl == 0 && c < n) {
         double t = acc;
         for (int r = 1; r < nrl; ++r) t += red[r * cw + cl];
         out[c] = t;
       }
     }
-    __syncthreads();
+    group_sync<NT>();
   }
 }
 
@@ -534,6 +552,7 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
   double *su = reinterpret_cast<double *>(sm + lay.su);
   double *Vs = reinterpret_cast<double *>(sm + lay.Vs);
   double *red4 = reinterpret_cast<double *>(sm + lay.red4);
+  double *cscr = reinterpret_cast<double *>(sm + lay.cscr);
   void *ys = sm + lay.ys;
   int *perm = reinterpret_cast<int *>(sm + lay.perm);
   int *posof = reinterpret_cast<int *>(sm + lay.posof);
@@ -574,7 +593,7 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
   // ---- initial column norms and the first pivot
   {
     double *rp = red + (size_t)par * L;
-    ccolsum<AT, true>(a, As, ncache, r0, 0, nrows, ys, red4, rp);
+    ccolsum<AT, true, kCT>(a, As, ncache, r0, 0, nrows, ys, cscr, rp);
     for (int q = (int)n + tid; q < L; q += kCT) rp[q] = 0.0;
     __syncthreads();
     if (!allreduce(a, cl, tm, rp, svo, svs, par, &s_ok, red4)) return cbail(a);
@@ -621,47 +640,52 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
     double *rp = red + (size_t)par * L;
     red4[tid] = s2;
     __syncthreads();
-    // V^T y over this block's rows below row j (j < 32): lanes = (row group g, column l)
-    // with the group width P the power of two >= j, so few FP64 lanes idle
-    if (j > 0) {
-      const int P = j <= 1 ? 1 : j <= 2 ? 2 : j <= 4 ? 4 : j <= 8 ? 8 : j <= 16 ? 16 : 32;
-      const int G = 32 / P, g = lane / P, l = lane % P;
-      double u = 0.0;
-      const int64_t lo = max((int64_t)0, (int64_t)j + 1 - r0);
-      for (int64_t li = lo + (int64_t)warp * G + g; li < nrows; li += (int64_t)kCW * G) {
-        const double *vr = Vs + li * kp;
-        if (l < j) u = fma(vr[l], vr[j], u);
+    if (tid < kColT) {
+      // A^T y over this block's rows from row j on (FP32 pipe)
+      ccolsum<AT, false, kColT>(a, As, ncache, r0, max((int64_t)0, (int64_t)j - r0), nrows, ys, cscr, rp);
+    } else {
+      // meanwhile, on the FP64 pipe: V^T y over this block's rows below row j (j < 32), lanes =
+      // (row group g, column l) with the group width P the power of two >= j; ||y||^2; row j of V
+      const int aw = warp - kColT / 32, at = tid - kColT;  // auxiliary warp 0 .. kAuxT/32 - 1
+      constexpr int kAuxW = kAuxT / 32;
+      if (j > 0) {
+        const int P = j <= 1 ? 1 : j <= 2 ? 2 : j <= 4 ? 4 : j <= 8 ? 8 : j <= 16 ? 16 : 32;
+        const int G = 32 / P, g = lane / P, l = lane % P;
+        double u = 0.0;
+        const int64_t lo = max((int64_t)0, (int64_t)j + 1 - r0);
+        for (int64_t li = lo + (int64_t)aw * G + g; li < nrows; li += (int64_t)kAuxW * G) {
+          const double *vr = Vs + li * kp;
+          if (l < j) u = fma(vr[l], vr[j], u);
+        }
+        for (int o = P; o < 32; o <<= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+        if (g == 0) red4[kCT + aw * 32 + l] = u;  // [0, kCT) holds the ||y||^2 partials
       }
-      for (int o = P; o < 32; o <<= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
-      if (g == 0) red4[kCT + warp * 32 + l] = u;  // [0, kCT) holds the ||y||^2 partials
-    }
-    __syncthreads();
-    if (warp == 0) {  // ||y||^2 partial: a tree over each lane's 16 entries (lane + 32 q: no bank
-                      // conflicts), then over the lanes
+      // ||y||^2: a tree over each thread's kCT / kAuxT partials, then over the lanes and warps
       double x[16];
 #pragma unroll
-      for (int q = 0; q < kCW; ++q) x[q] = red4[q * 32 + lane];
-      double t = tree16(x);
+      for (int q = 0; q < 16; ++q) x[q] = (q < kCT / kAuxT) ? red4[q * kAuxT + at] : 0.0;
+      double s = tree16(x);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      if (lane == 0) {
-        rp[n + k] = t;
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) red4[kCT + 64 + aw] = s;
+      asm volatile("bar.sync 2, %0;\n" ::"r"(kAuxT) : "memory");
+      if (at == 0) {
+        double tt = red4[kCT + 64];
+        for (int w2 = 1; w2 < kAuxW; ++w2) tt += red4[kCT + 64 + w2];
+        rp[n + k] = tt;
         rp[n + k + 1] = owner ? Vs[(j - r0) * kp + j] : 0.0;
       }
-    }
-    for (int q = tid - 32; q >= 0 && q < k; q += kCT) {  // warps 1..: V^T y (a tree over the warps), row j of V
-      double t = 0.0;
-      if (q < j) {
-        double x[16];
-#pragma unroll
-        for (int w = 0; w < kCW; ++w) x[w] = red4[kCT + w * 32 + q];
-        t = tree16(x);
+      for (int q = at; q < k; q += kAuxT) {
+        double tt = 0.0;
+        if (q < j) {
+          tt = red4[kCT + q];
+          for (int w2 = 1; w2 < kAuxW; ++w2) tt += red4[kCT + w2 * 32 + q];
+        }
+        rp[n + q] = tt;
+        rp[n + k + 2 + q] = (owner && q < j) ? Vs[(j - r0) * kp + q] : 0.0;
       }
-      rp[n + q] = t;
-      rp[n + k + 2 + q] = (owner && q < j) ? Vs[(j - r0) * kp + q] : 0.0;
     }
-    // A^T y over this block's rows from row j on (its first barrier orders the above)
-    ccolsum<AT, false>(a, As, ncache, r0, max((int64_t)0, (int64_t)j - r0), nrows, ys, red4, rp);
+    __syncthreads();
     if (!allreduce(a, cl, tm, rp, svo, svs, par, &s_ok, red4)) return cbail(a);
     par ^= 1;
 
