@@ -217,7 +217,7 @@ tucker_status launch_loss_grad(Ctx *c, const float *const *U, const float *G, do
   for (int n = 0; n < N; ++n) {
     const ModeCopy &mc = c->mode[n];
     const float *en = c->adj_e0;
-    if (n > 0 && Z > 0) {
+    if (mc.src && Z > 0) {  // this mode's order is not the lexicographic one
       adj_gather_kernel<<<blocks_for(Z, 4096), 256, 0, s>>>(Z, mc.src, c->adj_e0, c->adj_en);
       ::tk::count_launch();
       en = c->adj_en;

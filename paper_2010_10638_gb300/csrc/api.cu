@@ -150,7 +150,8 @@ static tucker_status init_impl(Ctx *c, const uint32_t *coords, const float *vals
     for (int n = 0; n < N; ++n)
       if (c->mode[n].fib) {
         fmax = std::max(fmax, c->mode[n].F);
-        tmax = std::max(tmax, c->mode[n].F * (int64_t)c->ranks[c->mode[n].other[c->mode[n].nother - 1]]);
+        const ModeCopy &mc = c->mode[n];  // t_f sums the remaining mode that is not the middle one
+        tmax = std::max(tmax, mc.F * (int64_t)c->ranks[mc.other[1 - mc.fmid_t]]);
       }
     if (fmax > 0) {
       TK_CUDA(dev_alloc(c, &c->fib_T, (size_t)tmax));

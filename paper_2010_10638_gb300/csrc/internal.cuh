@@ -45,9 +45,11 @@ struct ModeCopy {
   uint32_t *src = nullptr;             // [nnz] coalesced (lexicographic) index of sorted position e;
                                        // nullptr for mode 1, whose order is the lexicographic one
   // Fiber level (order 3): within a slice, runs of nonzeros with the same index of the
-  // first remaining mode, cut every kFiberCap nonzeros.  Work units and long-slice tables
-  // over fibers, as above over nonzeros.
+  // middle remaining mode other[fmid_t], cut every kFiberCap nonzeros (with fmid_t = 1 the
+  // copy is sorted by (i_n, i_other[1], i_other[0])).  Work units and long-slice tables over
+  // fibers, as above over nonzeros.
   bool fib = false;
+  int fmid_t = 0;                      // the middle (fiber) level is remaining mode other[fmid_t]
   int64_t F = 0;                       // fibers
   uint32_t *fptr = nullptr;            // [F+1] first sorted position of each fiber
   uint32_t *fmid = nullptr;            // [F] index of the first remaining mode of each fiber

@@ -316,6 +316,11 @@ __global__ void gather_mode_kernel(int64_t n, const uint32_t *perm, GatherArgs g
   }
 }
 
+__global__ void row_kernel(int64_t n, const uint32_t *perm, const uint32_t *rowsrc, uint32_t *row) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    row[e] = rowsrc[perm ? perm[e] : (uint32_t)e];
+}
+
 __global__ void iota_kernel(int64_t n, uint32_t *out) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
     out[e] = (uint32_t)e;
@@ -619,6 +624,7 @@ tucker_status build_sorted_copies(Ctx *c, const uint32_t *coords_in, const float
   TK_TRY(tmp.get(&islong, std::max<int64_t>(Z, 1) + 1));
   TK_TRY(tmp.get(&uoff, std::max<int64_t>(Z, 1) + 1));
   TK_TRY(tmp.get(&lid, std::max<int64_t>(Z, 1) + 1));
+  uint32_t fnat[kMaxOrder] = {};  // natural fiber counts, middle = first remaining mode
   uint32_t *fnstart = nullptr, *fcut = nullptr, *fcpos = nullptr;
   if (N == 3 && fiber_policy() != 0) {
     TK_TRY(tmp.get(&fnstart, std::max<int64_t>(Z, 1)));
@@ -698,53 +704,99 @@ tucker_status build_sorted_copies(Ctx *c, const uint32_t *coords_in, const float
       tucker_status st2 = build_units(c, S, mc.sptr, mc.chunk, nu, islong, uoff, lid, stmp, d_small, o, s);
       if (st2 != TUCKER_OK) return st2;
     }
-    // fiber level (order 3)
-    const int fp = fiber_policy();
-    if (N == 3 && Z > 0 && S > 0 && fp != 0) {
+    // natural fiber count with the first remaining mode as the middle level (order 3)
+    if (N == 3 && Z > 0 && S > 0 && fiber_policy() != 0) {
       fiber_flag_kernel<<<grid_for(Z), 256, 0, s>>>(Z, row, mc.idx[0], flag);
       ::tk::count_launch();
       exclusive_scan_total(flag, pos, Z, stmp, d_small + 4, s);
-      fiber_nstart_kernel<<<grid_for(Z), 256, 0, s>>>(Z, flag, pos, fnstart);
-      ::tk::count_launch();
-      uint32_t cap = (uint32_t)kFiberCap;
-      if (const char *fc = std::getenv("TUCKER_TTMC_FIBER_CAP")) {
-        const int v = std::atoi(fc);
-        if (v >= 1 && v <= kFiberCap) cap = (uint32_t)v;
-      }
-      fiber_cut_kernel<<<grid_for(Z), 256, 0, s>>>(Z, flag, pos, fnstart, cap, fcut);
-      ::tk::count_launch();
-      exclusive_scan_total(fcut, fcpos, Z, stmp, d_small + 5, s);
-      uint32_t F = 0;
-      tucker_status st2 = read_u32(c, d_small + 5, &F, s);
+      uint32_t fn = 0;
+      tucker_status st2 = read_u32(c, d_small + 4, &fn, s);
       if (st2 != TUCKER_OK) return st2;
-      if (fp == 1 || (double)F <= kFiberShare * (double)Z) {
-        mc.fib = true;
-        mc.F = F;
-        TK_TRY(dev_alloc(c, &mc.fptr, (size_t)F + 1));
-        TK_TRY(dev_alloc(c, &mc.fmid, (size_t)std::max<uint32_t>(F, 1)));
-        TK_TRY(dev_alloc(c, &mc.fsptr, (size_t)S + 1));
-        fiber_write_kernel<<<grid_for(Z), 256, 0, s>>>(Z, fcut, fcpos, mc.idx[0], mc.fptr, mc.fmid, F);
+      fnat[n] = fn;
+    }
+  }
+
+  // ---- fiber levels (order 3).  The middle level of mode n is its first remaining mode a,
+  //      or its last one b when the copy of b is grouped by (i_b, i_n) and has at most 0.8
+  //      as many (i_n, i_b) runs as mode n has (i_n, i_a) runs: then mode n's copy is
+  //      re-sorted to (i_n, i_b, i_a) (slices and nonzero units are unchanged).
+  const int fp = fiber_policy();
+  for (int n = 0; n < N && N == 3 && Z > 0 && fp != 0; ++n) {
+    ModeCopy &mc = c->mode[n];
+    if (mc.S == 0) continue;
+    const int b = mc.other[1];
+    const bool alt = c->mode[b].other[0] == n && fnat[b] > 0 && (double)fnat[b] <= 0.8 * (double)fnat[n];
+    uint32_t *perm = nullptr;
+    if (alt) {  // stable sorts of the lexicographic list by i_b, then by i_n
+      radix_sort_perm(c->coords + (int64_t)b * Z, bits_for(c->dims[b] - 1), Z, &perm, pa, pb, hist, stmp, s);
+      radix_sort_perm(c->coords + (int64_t)n * Z, bits_for(mc.I - 1), Z, &perm, pa, pb, hist, stmp, s);
+      if (!mc.src) TK_TRY(dev_alloc(c, &mc.src, (size_t)Z));
+      if (perm) {
+        TK_TRY(cudaMemcpyAsync(mc.src, perm, sizeof(uint32_t) * (size_t)Z, cudaMemcpyDeviceToDevice, s));
+      } else {
+        iota_kernel<<<grid_for(Z), 256, 0, s>>>(Z, mc.src);
         ::tk::count_launch();
-        fiber_slices_kernel<<<grid_for(S), 256, 0, s>>>(S, mc.sptr, fcpos, mc.fsptr, F);
-        ::tk::count_launch();
-        TK_TRY(cudaGetLastError());
-        // a fiber unit spans about as many nonzeros as a nonzero unit (a fiber costs its
-        // nonzeros plus one rank-1 update), in multiples of 32 fibers
-        {
-          const double per = (double)mc.chunk * (double)F / (double)Z;
-          int fc = (int)(per / 32.0) * 32;
-          mc.fchunk = std::max(64, std::min(2048, fc));
-          const char *f = std::getenv("TUCKER_TTMC_FCHUNK");
-          if (f) {
-            const int v = std::atoi(f);
-            if (v >= 32 && v <= (1 << 20) && (v % 32) == 0) mc.fchunk = v;
-          }
-        }
-        UnitTables o{&mc.funit_e0, &mc.funit_k0, &mc.flong_k, &mc.flong_u0, &mc.flong_np, &mc.funit_slot,
-                     &mc.fn_units, &mc.fn_long};
-        st2 = build_units(c, S, mc.fsptr, mc.fchunk, nu, islong, uoff, lid, stmp, d_small, o, s);
-        if (st2 != TUCKER_OK) return st2;
       }
+      GatherArgs g{};
+      g.nother = mc.nother;
+      for (int q = 0; q < mc.nother; ++q) {
+        g.src[q] = c->coords + (int64_t)mc.other[q] * Z;
+        g.dst[q] = mc.idx[q];
+      }
+      gather_mode_kernel<<<grid_for(Z), 256, 0, s>>>(Z, perm, g, c->coords + (int64_t)n * Z, row, c->vals, mc.val);
+      ::tk::count_launch();
+    } else {  // the rows of this mode's order
+      row_kernel<<<grid_for(Z), 256, 0, s>>>(Z, mc.src, c->coords + (int64_t)n * Z, row);
+      ::tk::count_launch();
+    }
+    const int ft = alt ? 1 : 0;
+    const uint32_t *mid = mc.idx[ft];
+    fiber_flag_kernel<<<grid_for(Z), 256, 0, s>>>(Z, row, mid, flag);
+    ::tk::count_launch();
+    exclusive_scan_total(flag, pos, Z, stmp, d_small + 4, s);
+    fiber_nstart_kernel<<<grid_for(Z), 256, 0, s>>>(Z, flag, pos, fnstart);
+    ::tk::count_launch();
+    uint32_t cap = (uint32_t)kFiberCap;
+    if (const char *fc = std::getenv("TUCKER_TTMC_FIBER_CAP")) {
+      const int v = std::atoi(fc);
+      if (v >= 1 && v <= kFiberCap) cap = (uint32_t)v;
+    }
+    fiber_cut_kernel<<<grid_for(Z), 256, 0, s>>>(Z, flag, pos, fnstart, cap, fcut);
+    ::tk::count_launch();
+    exclusive_scan_total(fcut, fcpos, Z, stmp, d_small + 5, s);
+    uint32_t F = 0;
+    tucker_status st2 = read_u32(c, d_small + 5, &F, s);
+    if (st2 != TUCKER_OK) return st2;
+    if (fp == 1 || (double)F <= kFiberShare * (double)Z) {
+      mc.fib = true;
+      mc.fmid_t = ft;
+      mc.F = F;
+      TK_TRY(dev_alloc(c, &mc.fptr, (size_t)F + 1));
+      TK_TRY(dev_alloc(c, &mc.fmid, (size_t)std::max<uint32_t>(F, 1)));
+      TK_TRY(dev_alloc(c, &mc.fsptr, (size_t)mc.S + 1));
+      fiber_write_kernel<<<grid_for(Z), 256, 0, s>>>(Z, fcut, fcpos, mid, mc.fptr, mc.fmid, F);
+      ::tk::count_launch();
+      fiber_slices_kernel<<<grid_for(mc.S), 256, 0, s>>>(mc.S, mc.sptr, fcpos, mc.fsptr, F);
+      ::tk::count_launch();
+      TK_TRY(cudaGetLastError());
+      // a fiber unit spans about as many nonzeros as a nonzero unit (a fiber costs its
+      // nonzeros plus one rank-1 update), in multiples of 32 fibers
+      {
+        const double per = (double)mc.chunk * (double)F / (double)Z;
+        int fc = (int)(per / 32.0) * 32;
+        mc.fchunk = std::max(64, std::min(2048, fc));
+        const char *f = std::getenv("TUCKER_TTMC_FCHUNK");
+        if (f) {
+          const int v = std::atoi(f);
+          if (v >= 32 && v <= (1 << 20) && (v % 32) == 0) mc.fchunk = v;
+        }
+      }
+      UnitTables o{&mc.funit_e0, &mc.funit_k0, &mc.flong_k, &mc.flong_u0, &mc.flong_np, &mc.funit_slot,
+                   &mc.fn_units, &mc.fn_long};
+      st2 = build_units(c, mc.S, mc.fsptr, mc.fchunk, nu, islong, uoff, lid, stmp, d_small, o, s);
+      if (st2 != TUCKER_OK) return st2;
+    } else if (alt) {  // keep the re-sorted copy: the nonzero form does not depend on the order
+      mc.fmid_t = 0;
     }
   }
   TK_TRY(cudaStreamSynchronize(s));

@@ -1302,12 +1302,17 @@ static tucker_status ttmc_impl(Ctx *c, int mode, float *Y, const float *val, con
     q.fptr = mc.fptr;
     q.fmid = mc.fmid;
     cudaError_t err = cudaSuccess;
-    if (dispatch_fibsum(q, c->fib_T, c->nnz, s, &err)) {
+    const int ft = mc.fmid_t;  // middle level: remaining mode other[ft]; t_f sums other[1 - ft]
+    TtmcParams qs = q;         // the fiber-sum pass reads the summed mode as its "last" mode
+    qs.idx[1] = q.idx[1 - ft];
+    qs.U[1] = q.U[1 - ft];
+    qs.R[1] = q.R[1 - ft];
+    if (dispatch_fibsum(qs, c->fib_T, c->nnz, s, &err)) {
       TK_CUDA(err);
-      TtmcParams r = q;  // the fibers as nonzeros: rows U_a(fmid[f]) and t_f, value 1
-      r.idx[0] = mc.fmid;
-      r.idx[1] = c->fib_iota;
-      r.U[1] = c->fib_T;
+      TtmcParams r = q;  // the fibers as nonzeros, value 1: rows t_f and the middle mode's rows
+      r.idx[ft] = mc.fmid;
+      r.idx[1 - ft] = c->fib_iota;
+      r.U[1 - ft] = c->fib_T;
       r.val = c->fib_ones;
       dispatch_pipe(r, s, &err);  // covers the shape (checked above)
       TK_CUDA(err);

@@ -29,6 +29,10 @@ CASES = [
     ("r32", (40, 32, 100), (32, 32, 32), 12_007, "uniform"),
     ("dense-ish", (30, 30, 30), (16, 16, 16), 20_000, "distinct"),
     ("single-slice", (1, 50, 400), (1, 16, 16), 20_011, "uniform"),
+    # mode 1's slices repeat the index of mode 3 far more than that of mode 2: its copy is
+    # re-sorted so that mode 3 is the middle level
+    ("middle-last-r16-r8", (60, 2000, 12), (16, 16, 8), 40_009, "uniform"),
+    ("middle-last-r16", (50, 3000, 16), (16, 16, 16), 30_011, "uniform"),
 ]
 
 
@@ -84,12 +88,14 @@ def test_fiber_form_is_deterministic(monkeypatch):
         np.testing.assert_array_equal(a, b)
 
 
-def test_fiber_form_in_the_adjoint(monkeypatch):
-    """The loss gradient runs the TTMc of the residual tensor through the same form."""
+@pytest.mark.parametrize("dims", [(40, 8, 60), (40, 60, 8)], ids=["middle-first", "middle-last"])
+def test_fiber_form_in_the_adjoint(monkeypatch, dims):
+    """The loss gradient runs the TTMc of the residual tensor through the same form
+    (including a mode whose copy is re-sorted for its fiber level)."""
     monkeypatch.setenv("TUCKER_TTMC_FIBERS", "1")
     from tests.test_gpu_adjoint import gpu_loss_grad
     rng = np.random.default_rng(29)
-    dims, ranks = (40, 8, 60), (8, 8, 8)  # shapes the fiber form covers
+    ranks = (8, 8, 8)  # shapes the fiber form covers
     coords = draw(rng, dims, 4_000, "uniform")
     vals = rng.standard_normal(4_000).astype(np.float32)
     U = [rng.standard_normal((d, r)).astype(np.float32) for d, r in zip(dims, ranks)]
