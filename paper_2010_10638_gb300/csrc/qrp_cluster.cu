@@ -49,6 +49,10 @@ constexpr unsigned long long kCSpin = 1ull << 25;  // polls before a barrier wai
 // kCT - kColT threads form V^T y and ||y||^2 (FP64 pipe), each group with its own barrier.
 constexpr int kColT = 448;
 constexpr int kAuxT = kCT - kColT;
+// the auxiliary warps keep their V^T y partials in red4[kCT, kCT + 64) and their ||y||^2
+// sums from red4[kCT + 64] on: at most two of them (448 / 64 measured fastest of 480 / 32
+// and 448 / 64)
+static_assert(kAuxT == 32 || kAuxT == 64, "one or two auxiliary warps");
 
 // barrier of the first NT threads of the block (all of them: __syncthreads)
 template <int NT>
