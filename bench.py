@@ -554,6 +554,67 @@ def run_table3(args):
     return 0
 
 
+def run_configs(args):
+    """Every workload recipe at full size: GPU sweep and per-mode TTMc times (CUDA events),
+    HBM and arithmetic fractions of the TTMc, and the oracle's time per sweep (one sweep on
+    at most `oracle_nnz` entries, scaled by the nonzero count).  Parity at these sizes is
+    the GPU test suite's (sampled rows against the oracle, componentwise bound)."""
+    import torch
+    import oracle
+    from paper_2010_10638_gb300 import build as libbuild, synth, tucker as T
+    libbuild.build()
+    T.load()
+    oracle.build()
+    hbm_peak, _ = peaks()
+    bf16_peak = 1918.6
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            bf16_peak = float(json.load(f).get("bf16_tflops", bf16_peak))
+    except (OSError, ValueError):
+        pass
+    rows = []
+    for name in ("tiny-100^3", "zipf-10k^3", "order4-5M", "skew-20M"):
+        inst = synth.make(name)
+        w = inst.workload
+        N = len(w.dims)
+        for bf16 in ((False, True) if name in ("order4-5M", "skew-20M") else (False,)):
+            ctx = T.tucker_init(w.dims, torch.as_tensor(inst.coords.astype(np.int32)).cuda(),
+                                torch.as_tensor(inst.vals).cuda(), w.ranks, [torch.as_tensor(u).cuda() for u in inst.U0],
+                                bf16=bf16)
+            Zc = T.tucker_nnz(ctx)
+            T.tucker_set_profiling(ctx, True)
+            T.hooi_iter(ctx)
+            for _ in range(3):
+                T.hooi_iter(ctx)
+            ph = []
+            for _ in range(10):
+                T.hooi_iter(ctx)
+                ph.append(T.tucker_phase_times(ctx))
+            med = [float(np.median([p_[i] for p_ in ph])) for i in range(2 * N + 1)]
+            sweep_ms = sum(med)
+            ttmc_ms = [med[2 * n] for n in range(N)]
+            flops = [2.0 * ctx.P(n) * Zc for n in range(N)]
+            bytes_alg = [4.0 * N * Zc + 4.0 * w.dims[n] * ctx.P(n) + 4.0 * (w.dims[n] + 1) for n in range(N)]
+            gbs = sum(bytes_alg) / (sum(ttmc_ms) * 1e-3) / 1e9
+            tflops = sum(flops) / (sum(ttmc_ms) * 1e-3) / 1e12
+            T.tucker_free(ctx)
+            row = {"config": name, "form": "bf16 factors" if bf16 else "fp32", "nnz": Zc,
+                   "ttmc_nnz_per_s_per_mode": [Zc / (m_ * 1e-3) for m_ in ttmc_ms], "ttmc_ms": ttmc_ms,
+                   "hooi_s_per_iter": sweep_ms * 1e-3, "ttmc_hbm_gbs": gbs, "ttmc_hbm_frac": gbs / hbm_peak}
+            if bf16:
+                row["ttmc_tensor_frac"] = tflops / bf16_peak
+            else:
+                row["ttmc_fp32_frac"] = tflops / FP32_PEAK_TFLOPS
+            if not bf16:
+                t_s, nz = oracle_sample(inst, min(args.oracle_nnz, w.nnz))
+                row["oracle_s_per_iter"] = t_s * Zc / nz
+                row["oracle_note"] = ("full sweep" if nz >= Zc else f"one sweep on {nz:,} entries, scaled to {Zc:,}")
+                row["oracle_cores"] = 1
+            rows.append(row)
+    print(json.dumps({"experiment": "all workload recipes", "rows": rows}), flush=True)
+    return 0
+
+
 def _stream(s):
     return int(s.cuda_stream)
 
@@ -572,7 +633,10 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--fig7", action="store_true", help="Fig. 7 sparsity sweep (200^3, ranks 16) instead")
     ap.add_argument("--table3", action="store_true", help="Table III core TTM shapes instead")
+    ap.add_argument("--configs", action="store_true", help="every workload recipe at full size instead")
     args = ap.parse_args()
+    if args.configs:
+        return run_configs(args)
     if args.fig7:
         return run_fig7(args)
     if args.table3:
