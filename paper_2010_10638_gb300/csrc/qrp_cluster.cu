@@ -20,8 +20,10 @@
 //            cluster barrier every block takes the best proposal (lowest position on
 //            ties), so all copies of the column order stay identical.
 // A^T v_j is A^T y + (v_jj - y_jj) A[j, :] (v_j differs from y only in row j), so the
-// pass over A starts before the reflector is known.  FP32 A: exact products summed in
-// double-float pairs (dfloat.cuh) and converted to FP64 once per column; FP64 A: FMA.
+// pass over A starts before the reflector is known.  FP32 A: the column norms are exact
+// products summed in double-float pairs (dfloat.cuh); A^T y is summed around power-of-two
+// offsets chosen from those norms (off_fma), eight FP32 operations per product with the
+// rounding residuals kept; each column's sum is converted to FP64 once.  FP64 A: FMA.
 // The FP64 pipe is narrow on this GPU, so FP64 work is kept to what the method needs
 // and is not issued for idle lanes in long loops.  Downdated norms that lose more than
 // sqrt(eps) of their last exact value are recomputed exactly (rare).
@@ -54,6 +56,16 @@ constexpr int kAuxT = kCT - kColT;
 // and 448 / 64)
 static_assert(kAuxT == 32 || kAuxT == 64, "one or two auxiliary warps");
 
+// Threads per row of A in the FP32 column sums (one column quad per thread): the power of
+// two from 8 up to the number of quads nq, at most nt; the remaining threads form nt / cw
+// row lanes.  The norm pass and the A^T y passes use the same layout, so a thread keeps the
+// same rows and columns in both.
+__host__ __device__ inline int quad_cw(int64_t nq, int nt) {
+  int cw = 8;
+  while (cw < nq && cw * 2 <= nt) cw <<= 1;
+  return cw;
+}
+
 // barrier of the first NT threads of the block (all of them: __syncthreads)
 template <int NT>
 __device__ __forceinline__ void group_sync() {
@@ -84,8 +96,8 @@ struct CArgs {
 
 // Dynamic shared memory of one block; the same arithmetic on host and device.
 struct CLayout {
-  size_t Fo, vno, vrefo, ajo, svo, svs, flago, doneo, red, Ts, Vt, Ms, su, Vs, red4, cscr, ys, perm, posof, cand, As,
-      total;
+  size_t Fo, vno, vrefo, ajo, svo, svs, flago, doneo, red, Ts, Vt, Ms, su, Vs, red4, cscr, nat, ys, perm, posof, cand,
+      As, total;
   int kp;      // row stride of Vs in doubles (odd: rows fall in different banks)
   int64_t no;  // columns per block, rounded up
 };
@@ -114,7 +126,13 @@ __host__ __device__ inline CLayout clayout(int64_t n, int k, int L, int S, int64
   l.su = o;    o += c16(sizeof(double) * 64);
   l.Vs = o;    o += c16(sizeof(double) * (size_t)rows_per * l.kp);  // this block's rows of V
   l.red4 = o;  o += c16(sizeof(double) * 2 * kCT);        // reduction scratch (8 KB)
-  l.cscr = o;  o += c16(sizeof(double) * 2 * kCT);        // column-sum scratch (8 KB)
+  l.cscr = o;  // column-sum scratch: 2 x kCT doubles, or 4 x kColT double-float pairs
+  o += c16(sizeof(double) * 2 * kCT > sizeof(float) * 8 * kColT ? sizeof(double) * 2 * kCT : sizeof(float) * 8 * kColT);
+  l.nat = o;   // FP32 A: per thread and column quad, bounds on the norms of its pieces of 4 columns
+  if (esize == 4 && n % 4 == 0) {
+    const int64_t nq = n / 4, cw = quad_cw(nq, kColT);
+    o += c16(sizeof(float) * 4 * (size_t)kColT * (size_t)((nq + cw - 1) / cw));
+  }
   l.ys = o;    o += c16(sizeof(double) * (size_t)rows_per);  // y per row (float2 or double)
   l.perm = o;  o += c16(sizeof(int) * (size_t)n);
   l.posof = o; o += c16(sizeof(int) * (size_t)n);
@@ -326,6 +344,79 @@ __device__ __forceinline__ void seg4(const float4 *base, int64_t stride4, int64_
   }
 }
 
+// Offset accumulation of sum_i a_i (bh_i + bl_i) (FP32 a, FP64 y split into bh + bl), used
+// for A^T y.  With B >= |every partial sum of a_i bh_i| and s1 a power of two > 2B, the
+// running sum hi = s1 + (partial) stays in [s1/2, 3 s1/2]: every hi is a multiple of
+// ulp(s1/2), so hi - t below is exact, and t = fma(a, bh, hi) rounds a_i bh_i onto that grid
+// with residual r = a_i bh_i + hi - t (computed by a second FMA, to 2^-24 of |r|).  The
+// residuals (each below 2^-24 s1) are summed exactly the same way around a second power of
+// two s2 (Fast2Sum against a much larger addend), and only the residuals of that sum and
+// the bl terms (2^-24 below the bh terms) are summed in plain FP32.  Eight FP32 operations
+// per product instead of the twelve of a double-float sum; the error stays at about
+// 2^-49 s1 per product.  B comes from Cauchy-Schwarz: ||a|| ||bh|| over the thread's rows.
+struct OffAcc {
+  float hi, mid, lo;
+};
+
+__device__ __forceinline__ void off_fma(OffAcc &s, float a, float bh, float bl) {
+  const float t = fmaf(a, bh, s.hi);
+  const float r = fmaf(a, bh, s.hi - t);
+  const float t2 = s.mid + r;
+  const float r2 = r + (s.mid - t2);
+  s.lo = fmaf(a, bl, s.lo + r2);
+  s.hi = t;
+  s.mid = t2;
+}
+
+// s1: the power of two in (2 nb, 4 nb] (biased exponent + 2), kept inside the normal range
+__device__ __forceinline__ float off_s1(float nb) {
+  int e = (int)((__float_as_uint(nb) >> 23) & 0xffu) + 2;
+  e = e < 1 ? 1 : (e > 254 ? 254 : e);
+  return __uint_as_float((unsigned)e << 23);
+}
+
+// s2 for at most 2^lk residuals, each below 2^-24 s1: 4 times their largest possible sum
+__device__ __forceinline__ float off_s2(float s1, int lk) {
+  int e = (int)(__float_as_uint(s1) >> 23) - 22 + lk;
+  e = e < 1 ? 1 : e;
+  return __uint_as_float((unsigned)e << 23);
+}
+
+// Rows [s0, s1) (local indices, step nrl from s0 + rl) of four adjacent columns, eight
+// rows per batch with all loads issued first (in this kernel's register budget, deeper
+// batches keep more loads in flight: measured faster than four).  Row offsets are 32-bit:
+// a block's rows times the row stride stay far below 2^31.
+template <bool GLOBAL>
+__device__ __forceinline__ void seg4_off(const float4 *base, int stride4, int s0, int s1, int rl, int nrl,
+                                         const float2 *y2, OffAcc (&d)[4]) {
+  int ii = s0 + rl;
+  for (; ii + 7 * nrl < s1; ii += 8 * nrl) {
+    float4 x[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const float4 *p = base + (ii + u * nrl) * stride4;
+      x[u] = GLOBAL ? __ldg(p) : *p;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const float2 vv = y2[ii + u * nrl];
+      off_fma(d[0], x[u].x, vv.x, vv.y);
+      off_fma(d[1], x[u].y, vv.x, vv.y);
+      off_fma(d[2], x[u].z, vv.x, vv.y);
+      off_fma(d[3], x[u].w, vv.x, vv.y);
+    }
+  }
+  for (; ii < s1; ii += nrl) {
+    const float4 *p = base + ii * stride4;
+    const float4 x = GLOBAL ? __ldg(p) : *p;
+    const float2 vv = y2[ii];
+    off_fma(d[0], x.x, vv.x, vv.y);
+    off_fma(d[1], x.y, vv.x, vv.y);
+    off_fma(d[2], x.z, vv.x, vv.y);
+    off_fma(d[3], x.w, vv.x, vv.y);
+  }
+}
+
 __device__ __forceinline__ DF df_of(float2 p) {
   DF d;
   d.hi = p.x;
@@ -335,43 +426,95 @@ __device__ __forceinline__ DF df_of(float2 p) {
 
 // out[c], c < n: sum over local rows li in [l0, nrows) of A[r0 + li, c] * y_li (SQUARE:
 // A[r0 + li, c]^2).  Rows li < ncache come from the shared copy As (row stride n).
-// Run by the first NT threads (NT a multiple of 32); `scratch` holds 2 * NT doubles.
+// Run by the first NT threads (NT a multiple of 32); `scratch` holds 2 * NT doubles (and,
+// for FP32 A read as float4, 4 * NT double-float pairs).  FP32 A read as float4: the SQUARE
+// pass stores in `nat` each thread's bound on the norms of its pieces of its 4 columns
+// (quad layout of quad_cw), and the other passes use the offset accumulation with those
+// bounds; their partial sums are added over the row lanes in one round, the threads of
+// row lane c adding column c of every quad.
 template <typename AT, bool SQUARE, int NT>
 __device__ void ccolsum(const CArgs &a, const AT *As, int64_t ncache, int64_t r0, int64_t l0, int64_t nrows,
-                        const void *ys, void *scratch, double *out) {
+                        const void *ys, void *scratch, float *nat, double *out) {
   const int64_t n = a.n;
   const AT *A = static_cast<const AT *>(a.A);
   l0 = min(l0, nrows);
   if constexpr (sizeof(AT) == 4) {
-    float2 *red = static_cast<float2 *>(scratch);  // 2 x kCT double-float pairs
+    float2 *red = static_cast<float2 *>(scratch);
     const float2 *y2 = static_cast<const float2 *>(ys);
     if (a.vec4) {
       const int64_t nq = n / 4, ld4 = a.lda / 4, sn4 = n / 4;
-      int cw = 8;
-      while (cw < nq && cw * 2 <= NT) cw <<= 1;  // cw <= NT
+      const int cw = quad_cw(nq, NT);
       const int nrl = NT / cw, cq = threadIdx.x % cw, rl = threadIdx.x / cw;
       const bool act = rl < nrl;  // NT need not be a multiple of cw
-      for (int64_t q0 = 0; q0 < nq; q0 += cw) {
-        const int64_t qc = q0 + cq;
-        DF d[4];
-        if (act && qc < nq) {
-          seg4<false, SQUARE>(reinterpret_cast<const float4 *>(As) + qc, sn4, l0, min(nrows, ncache), rl, nrl, y2,
+      float4 *nat4 = reinterpret_cast<float4 *>(nat);
+      constexpr float kMargin = 1.0f + 1.0f / 256.0f;  // covers the FP32 rounding of the bounds
+      if constexpr (SQUARE) {
+        for (int64_t q0 = 0, it = 0; q0 < nq; q0 += cw, ++it) {
+          const int64_t qc = q0 + cq;
+          DF d[4];
+          if (act && qc < nq) {
+            seg4<false, true>(reinterpret_cast<const float4 *>(As) + qc, sn4, l0, min(nrows, ncache), rl, nrl, y2,
                               d[0], d[1], d[2], d[3]);
-          seg4<true, SQUARE>(reinterpret_cast<const float4 *>(A) + r0 * ld4 + qc, ld4, max(l0, ncache), nrows, rl,
+            seg4<true, true>(reinterpret_cast<const float4 *>(A) + r0 * ld4 + qc, ld4, max(l0, ncache), nrows, rl,
                              nrl, y2, d[0], d[1], d[2], d[3]);
+          }
+          if (nat && act)
+            nat4[it * NT + threadIdx.x] = make_float4(sqrtf(fmaxf(d[0].hi, 0.f)) * kMargin, sqrtf(fmaxf(d[1].hi, 0.f)) * kMargin,
+                                                      sqrtf(fmaxf(d[2].hi, 0.f)) * kMargin, sqrtf(fmaxf(d[3].hi, 0.f)) * kMargin);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {  // two columns of the four at a time through the scratch
+            group_sync<NT>();
+            red[threadIdx.x] = make_float2(d[2 * h].hi, d[2 * h].lo);
+            red[NT + threadIdx.x] = make_float2(d[2 * h + 1].hi, d[2 * h + 1].lo);
+            group_sync<NT>();
+            if (rl == 0 && qc < nq) {
+#pragma unroll
+              for (int q = 0; q < 2; ++q) {
+                DF t = d[2 * h + q];
+                for (int r = 1; r < nrl; ++r) df_add(t, df_of(red[q * NT + r * cw + cq]));
+                out[4 * qc + 2 * h + q] = (double)t.hi + (double)t.lo;
+              }
+            }
+          }
         }
+      } else {
+        // this thread's ||bh|| over its rows, and the number of rows it sums (for s2)
+        float ny2 = 0.f;
+        if (act)
+          for (int64_t li = l0 + rl; li < nrows; li += nrl) {
+            const float h = y2[li].x;
+            ny2 = fmaf(h, h, ny2);
+          }
+        const float sy = sqrtf(ny2) * kMargin;
+        const int lk = 64 - __clzll((nrows - l0 + nrl - 1) / nrl + 1);  // 2^lk > rows per thread
+        for (int64_t q0 = 0, it = 0; q0 < nq; q0 += cw, ++it) {
+          const int64_t qc = q0 + cq;
+          const bool mine = act && qc < nq;
+          const float4 nb = mine ? nat4[it * NT + threadIdx.x] : make_float4(0.f, 0.f, 0.f, 0.f);
+          const float s1[4] = {off_s1(nb.x * sy), off_s1(nb.y * sy), off_s1(nb.z * sy), off_s1(nb.w * sy)};
+          OffAcc d[4];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {  // two columns of the four at a time through the scratch
+          for (int c = 0; c < 4; ++c) {
+            d[c].hi = s1[c];
+            d[c].mid = off_s2(s1[c], lk);
+            d[c].lo = 0.f;
+          }
+          if (mine) {
+            seg4_off<false>(reinterpret_cast<const float4 *>(As) + qc, (int)sn4, (int)l0, (int)min(nrows, ncache), rl,
+                            nrl, y2, d);
+            seg4_off<true>(reinterpret_cast<const float4 *>(A) + r0 * ld4 + qc, (int)ld4, (int)max(l0, ncache),
+                           (int)nrows, rl, nrl, y2, d);
+          }
           group_sync<NT>();
-          red[threadIdx.x] = make_float2(d[2 * h].hi, d[2 * h].lo);
-          red[NT + threadIdx.x] = make_float2(d[2 * h + 1].hi, d[2 * h + 1].lo);
-          group_sync<NT>();
-          if (rl == 0 && qc < nq) {
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
-              DF t = d[2 * h + q];
-              for (int r = 1; r < nrl; ++r) df_add(t, df_of(red[q * NT + r * cw + cq]));
-              out[4 * qc + 2 * h + q] = (double)t.hi + (double)t.lo;
+          for (int c = 0; c < 4; ++c)  // hi - s1 and mid - s2 are exact (Sterbenz)
+            red[c * NT + threadIdx.x] = make_float2(d[c].hi - s1[c], (d[c].mid - off_s2(s1[c], lk)) + d[c].lo);
+          group_sync<NT>();
+          if (act && qc < nq) {
+            for (int c = rl; c < 4; c += nrl) {
+              DF t = df_of(red[c * NT + cq]);
+              for (int r = 1; r < nrl; ++r) df_add(t, df_of(red[c * NT + r * cw + cq]));
+              out[4 * qc + c] = (double)t.hi + (double)t.lo;
             }
           }
         }
@@ -557,6 +700,7 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
   double *Vs = reinterpret_cast<double *>(sm + lay.Vs);
   double *red4 = reinterpret_cast<double *>(sm + lay.red4);
   double *cscr = reinterpret_cast<double *>(sm + lay.cscr);
+  float *nat = reinterpret_cast<float *>(sm + lay.nat);
   void *ys = sm + lay.ys;
   int *perm = reinterpret_cast<int *>(sm + lay.perm);
   int *posof = reinterpret_cast<int *>(sm + lay.posof);
@@ -597,7 +741,8 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
   // ---- initial column norms and the first pivot
   {
     double *rp = red + (size_t)par * L;
-    ccolsum<AT, true, kCT>(a, As, ncache, r0, 0, nrows, ys, cscr, rp);
+    if (tid < kColT)  // the layout of the A^T y passes, which use the norm bounds it leaves in nat
+      ccolsum<AT, true, kColT>(a, As, ncache, r0, 0, nrows, ys, cscr, nat, rp);
     for (int q = (int)n + tid; q < L; q += kCT) rp[q] = 0.0;
     __syncthreads();
     if (!allreduce(a, cl, tm, rp, svo, svs, par, &s_ok, red4)) return cbail(a);
@@ -646,7 +791,7 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
     __syncthreads();
     if (tid < kColT) {
       // A^T y over this block's rows from row j on (FP32 pipe)
-      ccolsum<AT, false, kColT>(a, As, ncache, r0, max((int64_t)0, (int64_t)j - r0), nrows, ys, cscr, rp);
+      ccolsum<AT, false, kColT>(a, As, ncache, r0, max((int64_t)0, (int64_t)j - r0), nrows, ys, cscr, nat, rp);
     } else {
       // meanwhile, on the FP64 pipe: V^T y over this block's rows below row j (j < 32), lanes =
       // (row group g, column l) with the group width P the power of two >= j; ||y||^2; row j of V
@@ -964,7 +1109,11 @@ bool qrp_cluster(const AT *A, int64_t m, int64_t n, int64_t lda, int k, double *
   a.L = L;
   a.nclusters = C;
   a.cluster = S;
-  a.vec4 = (es == 4 && n % 4 == 0 && lda % 4 == 0 && (reinterpret_cast<uintptr_t>(A) % 16) == 0) ? 1 : 0;
+  // (the float4 column sums index a block's rows with 32-bit offsets)
+  a.vec4 = (es == 4 && n % 4 == 0 && lda % 4 == 0 && (reinterpret_cast<uintptr_t>(A) % 16) == 0 &&
+            rows_per * (lda / 4 + 1) < ((int64_t)1 << 31))
+               ? 1
+               : 0;
   a.rows_per = rows_per;
   a.rows_cached = rows_cached;
   a.slots = w->part;
