@@ -35,6 +35,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 
 #include "dfloat.cuh"
 #include "internal.cuh"
@@ -166,6 +167,46 @@ __device__ __forceinline__ void df_add(DF &a, const DF b) {
   a.lo = e - (a.hi - s);
 }
 
+// Entries of the reductions' partial vectors.  FP32 A: double-float pairs (x = hi,
+// y = lo), so that their sums over the blocks of a cluster and over the clusters run on
+// the FP32 pipe (the FP64 pipe issues one warp instruction per 16 cycles per SM here),
+// with about 2^-48 relative error per addition; each needed entry is converted to FP64
+// once at the end.  FP64 A (values of any FP64 magnitude): FP64.
+__device__ __forceinline__ float2 df2_of(double v) {
+  const float h = __double2float_rn(v);
+  return make_float2(h, __double2float_rn(v - (double)h));
+}
+__device__ __forceinline__ double df2_val(float2 p) { return (double)p.x + (double)p.y; }
+__device__ __forceinline__ float2 df2_add(float2 a, float2 b) {
+  DF x;
+  x.hi = a.x;
+  x.lo = a.y;
+  DF y;
+  y.hi = b.x;
+  y.lo = b.y;
+  df_add(x, y);
+  return make_float2(x.hi, x.lo);
+}
+
+template <typename PT>
+struct Part;
+template <>
+struct Part<float2> {
+  static __device__ __forceinline__ float2 of(double v) { return df2_of(v); }
+  static __device__ __forceinline__ double val(float2 p) { return df2_val(p); }
+  static __device__ __forceinline__ float2 add(float2 a, float2 b) { return df2_add(a, b); }
+  static __device__ __forceinline__ float2 zero() { return make_float2(0.f, 0.f); }
+};
+template <>
+struct Part<double> {
+  static __device__ __forceinline__ double of(double v) { return v; }
+  static __device__ __forceinline__ double val(double p) { return p; }
+  static __device__ __forceinline__ double add(double a, double b) { return a + b; }
+  static __device__ __forceinline__ double zero() { return 0.0; }
+};
+template <typename AT>
+using PartT = typename std::conditional<sizeof(AT) == 4, float2, double>::type;
+
 // Ordering key of a squared norm (>= 0): its bit pattern without the sign (so -0 = 0);
 // NaN gets -1 and is never preferred.  Integer compares keep argmax off the FP64 pipe.
 __device__ __forceinline__ long long norm_key(double v) {
@@ -203,27 +244,34 @@ __device__ __forceinline__ double tree16(double (&x)[16]) {
   return x[0];
 }
 
-template <int NS>
-__device__ __forceinline__ double peer_tree(cg::cluster_group &cl, double *mine, int q) {
-  double x[NS];
-#pragma unroll
-  for (int r = 0; r < NS; ++r) x[r] = cl.map_shared_rank(mine, (unsigned)r)[q];
+// the same tree over partial-vector entries
+template <int NS, typename PT>
+__device__ __forceinline__ PT ptree(PT (&x)[NS]) {
 #pragma unroll
   for (int w = 1; w < NS; w <<= 1)
 #pragma unroll
-    for (int i = 0; i < NS; i += 2 * w) x[i] += x[i + w];
+    for (int i = 0; i < NS; i += 2 * w) x[i] = Part<PT>::add(x[i], x[i + w]);
   return x[0];
+}
+
+template <int NS, typename PT>
+__device__ __forceinline__ PT peer_tree(cg::cluster_group &cl, PT *mine, int q) {
+  PT x[NS];
+#pragma unroll
+  for (int r = 0; r < NS; ++r) x[r] = cl.map_shared_rank(mine, (unsigned)r)[q];
+  return ptree<NS>(x);
 }
 
 // sum over the S blocks of the cluster (S a power of two, at most 16) of entry q of
 // their vectors `mine` (shared memory), in a fixed tree over the ranks; all S loads are
 // issued before the additions
-__device__ __forceinline__ double peer_sum(cg::cluster_group &cl, double *mine, unsigned S, int q) {
+template <typename PT>
+__device__ __forceinline__ PT peer_sum(cg::cluster_group &cl, PT *mine, unsigned S, int q) {
   switch (S) {
-    case 16: return peer_tree<16>(cl, mine, q);
-    case 8: return peer_tree<8>(cl, mine, q);
-    case 4: return peer_tree<4>(cl, mine, q);
-    case 2: return peer_tree<2>(cl, mine, q);
+    case 16: return peer_tree<16, PT>(cl, mine, q);
+    case 8: return peer_tree<8, PT>(cl, mine, q);
+    case 4: return peer_tree<4, PT>(cl, mine, q);
+    case 2: return peer_tree<2, PT>(cl, mine, q);
     default: return mine[q];
   }
 }
@@ -234,12 +282,13 @@ struct Team {
   unsigned epoch;  // grid-wide reductions so far
 };
 
-// Sums of the blocks' partial vectors `mine` (L doubles each, shared memory), in the
-// same order in every block: entries of this block's columns into svo, the scalar
-// entries n .. L-1 into svs.  `scratch` holds ceil(clusters / 16) x (entries needed)
-// doubles.  False when a wait timed out (then no block reads a peer's memory any more).
-__device__ bool allreduce(const CArgs &a, cg::cluster_group &cl, Team &tm, double *mine, double *svo, double *svs,
-                          int par, int *s_ok, double *scratch) {
+// Sums of the blocks' partial vectors `mine` (L double-float pairs each, shared memory),
+// in the same order in every block: entries of this block's columns into svo, the scalar
+// entries n .. L-1 into svs (FP64).  `scratch` holds ceil(clusters / 16) x (entries
+// needed) pairs.  False when a wait timed out (then no block reads a peer's memory any more).
+template <typename PT>
+__device__ bool allreduce(const CArgs &a, cg::cluster_group &cl, Team &tm, PT *mine, double *svo, double *svs,
+                          int par, int *s_ok, PT *scratch) {
   const int L = a.L, n = (int)a.n, ns = 2 * a.k + 2, need = tm.nown + ns;
   auto entry = [&](int t) { return t < tm.nown ? (int)tm.rank + (int)tm.S * t : n + (t - tm.nown); };
   auto store = [&](int t, double v) {
@@ -250,12 +299,12 @@ __device__ bool allreduce(const CArgs &a, cg::cluster_group &cl, Team &tm, doubl
   };
   cl.sync();  // every block of the cluster has written its partials
   if (a.nclusters == 1) {
-    for (int t = threadIdx.x; t < need; t += kCT) store(t, peer_sum(cl, mine, tm.S, entry(t)));
+    for (int t = threadIdx.x; t < need; t += kCT) store(t, Part<PT>::val(peer_sum(cl, mine, tm.S, entry(t))));
     __syncthreads();
     return true;  // `mine` alternates between two buffers: the next write cannot race these reads
   }
   const int cid = (int)(blockIdx.x / tm.S);
-  double *slot = a.slots + ((size_t)par * a.nclusters + cid) * L;
+  PT *slot = reinterpret_cast<PT *>(a.slots) + ((size_t)par * a.nclusters + cid) * L;
   const int per = (int)((L + tm.S - 1) / tm.S);
   const int q0 = (int)tm.rank * per, q1 = min(L, q0 + per);
   bool wrote = false;
@@ -276,23 +325,23 @@ __device__ bool allreduce(const CArgs &a, cg::cluster_group &cl, Team &tm, doubl
   // the cluster sums this block needs: thread (entry t, chunk h) adds the clusters
   // 16h .. 16h+15 of entry t in a fixed tree (one round trip for all of them), then the
   // chunk sums of each entry are added in chunk order
-  const double *base = a.slots + (size_t)par * a.nclusters * L;
+  const PT *base = reinterpret_cast<const PT *>(a.slots) + (size_t)par * a.nclusters * L;
   const int nch = (a.nclusters + 15) / 16;
   for (int idx = threadIdx.x; idx < need * nch; idx += kCT) {
     const int t = idx % need, h = idx / need, q = entry(t);
-    double x[16];
+    PT x[16];
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
       const int cc = 16 * h + u;
-      x[u] = (cc < a.nclusters) ? __ldcg(base + (size_t)cc * L + q) : 0.0;
+      x[u] = (cc < a.nclusters) ? __ldcg(base + (size_t)cc * L + q) : Part<PT>::zero();
     }
-    scratch[idx] = tree16(x);
+    scratch[idx] = ptree<16>(x);
   }
   __syncthreads();
   for (int t = threadIdx.x; t < need; t += kCT) {
-    double sum = scratch[t];
-    for (int h = 1; h < nch; ++h) sum += scratch[h * need + t];
-    store(t, sum);
+    PT sum = scratch[t];
+    for (int h = 1; h < nch; ++h) sum = Part<PT>::add(sum, scratch[h * need + t]);
+    store(t, Part<PT>::val(sum));
   }
   __syncthreads();
   return true;
@@ -424,7 +473,8 @@ __device__ __forceinline__ DF df_of(float2 p) {
   return d;
 }
 
-// out[c], c < n: sum over local rows li in [l0, nrows) of A[r0 + li, c] * y_li (SQUARE:
+// out[c], c < n (a double-float pair): sum over local rows li in [l0, nrows) of
+// A[r0 + li, c] * y_li (SQUARE:
 // A[r0 + li, c]^2).  Rows li < ncache come from the shared copy As (row stride n).
 // Run by the first NT threads (NT a multiple of 32); `scratch` holds 2 * NT doubles (and,
 // for FP32 A read as float4, 4 * NT double-float pairs).  FP32 A read as float4: the SQUARE
@@ -434,7 +484,7 @@ __device__ __forceinline__ DF df_of(float2 p) {
 // row lane c adding column c of every quad.
 template <typename AT, bool SQUARE, int NT>
 __device__ void ccolsum(const CArgs &a, const AT *As, int64_t ncache, int64_t r0, int64_t l0, int64_t nrows,
-                        const void *ys, void *scratch, float *nat, double *out) {
+                        const void *ys, void *scratch, float *nat, PartT<AT> *out) {
   const int64_t n = a.n;
   const AT *A = static_cast<const AT *>(a.A);
   l0 = min(l0, nrows);
@@ -472,7 +522,7 @@ __device__ void ccolsum(const CArgs &a, const AT *As, int64_t ncache, int64_t r0
               for (int q = 0; q < 2; ++q) {
                 DF t = d[2 * h + q];
                 for (int r = 1; r < nrl; ++r) df_add(t, df_of(red[q * NT + r * cw + cq]));
-                out[4 * qc + 2 * h + q] = (double)t.hi + (double)t.lo;
+                out[4 * qc + 2 * h + q] = make_float2(t.hi, t.lo);
               }
             }
           }
@@ -514,7 +564,7 @@ __device__ void ccolsum(const CArgs &a, const AT *As, int64_t ncache, int64_t r0
             for (int c = rl; c < 4; c += nrl) {
               DF t = df_of(red[c * NT + cq]);
               for (int r = 1; r < nrl; ++r) df_add(t, df_of(red[c * NT + r * cw + cq]));
-              out[4 * qc + c] = (double)t.hi + (double)t.lo;
+              out[4 * qc + c] = make_float2(t.hi, t.lo);
             }
           }
         }
@@ -546,7 +596,7 @@ __device__ void ccolsum(const CArgs &a, const AT *As, int64_t ncache, int64_t r0
       if (rl == 0 && c < n) {
         DF t = d;
         for (int r = 1; r < nrl; ++r) df_add(t, df_of(red[r * cw + cl]));
-        out[c] = (double)t.hi + (double)t.lo;
+        out[c] = make_float2(t.hi, t.lo);
       }
     }
     group_sync<NT>();
@@ -692,6 +742,7 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
   double *svs = reinterpret_cast<double *>(sm + lay.svs);
   int *flago = reinterpret_cast<int *>(sm + lay.flago);
   int *doneo = reinterpret_cast<int *>(sm + lay.doneo);
+  using PT = PartT<AT>;  // entries of the partial vectors
   double *red = reinterpret_cast<double *>(sm + lay.red);
   double *Ts = reinterpret_cast<double *>(sm + lay.Ts);
   double *Vt = reinterpret_cast<double *>(sm + lay.Vt);
@@ -740,12 +791,12 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
 
   // ---- initial column norms and the first pivot
   {
-    double *rp = red + (size_t)par * L;
+    PT *rp = reinterpret_cast<PT *>(red) + (size_t)par * L;
     if (tid < kColT)  // the layout of the A^T y passes, which use the norm bounds it leaves in nat
       ccolsum<AT, true, kColT>(a, As, ncache, r0, 0, nrows, ys, cscr, nat, rp);
-    for (int q = (int)n + tid; q < L; q += kCT) rp[q] = 0.0;
+    for (int q = (int)n + tid; q < L; q += kCT) rp[q] = Part<PT>::zero();
     __syncthreads();
-    if (!allreduce(a, cl, tm, rp, svo, svs, par, &s_ok, red4)) return cbail(a);
+    if (!allreduce(a, cl, tm, rp, svo, svs, par, &s_ok, reinterpret_cast<PT *>(red4))) return cbail(a);
     par ^= 1;
     for (int lc = tid; lc < tm.nown; lc += kCT) {
       vno[lc] = svo[lc];
@@ -786,7 +837,7 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
         static_cast<double *>(ys)[li] = y;
       }
     }
-    double *rp = red + (size_t)par * L;
+    PT *rp = reinterpret_cast<PT *>(red) + (size_t)par * L;
     red4[tid] = s2;
     __syncthreads();
     if (tid < kColT) {
@@ -821,8 +872,8 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
       if (at == 0) {
         double tt = red4[kCT + 64];
         for (int w2 = 1; w2 < kAuxW; ++w2) tt += red4[kCT + 64 + w2];
-        rp[n + k] = tt;
-        rp[n + k + 1] = owner ? Vs[(j - r0) * kp + j] : 0.0;
+        rp[n + k] = Part<PT>::of(tt);
+        rp[n + k + 1] = Part<PT>::of(owner ? Vs[(j - r0) * kp + j] : 0.0);
       }
       for (int q = at; q < k; q += kAuxT) {
         double tt = 0.0;
@@ -830,12 +881,12 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
           tt = red4[kCT + q];
           for (int w2 = 1; w2 < kAuxW; ++w2) tt += red4[kCT + w2 * 32 + q];
         }
-        rp[n + q] = tt;
-        rp[n + k + 2 + q] = (owner && q < j) ? Vs[(j - r0) * kp + q] : 0.0;
+        rp[n + q] = Part<PT>::of(tt);
+        rp[n + k + 2 + q] = Part<PT>::of((owner && q < j) ? Vs[(j - r0) * kp + q] : 0.0);
       }
     }
     __syncthreads();
-    if (!allreduce(a, cl, tm, rp, svo, svs, par, &s_ok, red4)) return cbail(a);
+    if (!allreduce(a, cl, tm, rp, svo, svs, par, &s_ok, reinterpret_cast<PT *>(red4))) return cbail(a);
     par ^= 1;
 
     // ---- reflector (thread 0) while the column threads form the dot products that do not
@@ -920,8 +971,8 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
     __syncthreads();
     if (j + 1 < k && choose_pivot(cl, tm, j + 1, n, vno, flago, doneo, perm, posof, cand, &s_res)) {
       // exact norms of the flagged columns of the whole cluster (rare)
-      double *rq = red + (size_t)par * L;
-      for (int q = tid; q < L; q += kCT) rq[q] = 0.0;
+      PT *rq = reinterpret_cast<PT *>(red) + (size_t)par * L;
+      for (int q = tid; q < L; q += kCT) rq[q] = Part<PT>::zero();
       __syncthreads();
       for (unsigned q = 0; q < tm.S; ++q) {
         const int *pf = cl.map_shared_rank(flago, q);
@@ -947,12 +998,12 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
             for (int w = 0; w < kCW; ++w) u += red4[w * 32 + lane];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
-            if (lane == 0) rq[c] = u;
+            if (lane == 0) rq[c] = Part<PT>::of(u);
           }
           __syncthreads();
         }
       }
-      if (!allreduce(a, cl, tm, rq, svo, svs, par, &s_ok, red4)) return cbail(a);
+      if (!allreduce(a, cl, tm, rq, svo, svs, par, &s_ok, reinterpret_cast<PT *>(red4))) return cbail(a);
       par ^= 1;
       for (int lc = tid; lc < tm.nown; lc += kCT) {
         if (flago[lc]) {
