@@ -530,11 +530,21 @@ __device__ void ccolsum(const CArgs &a, const AT *As, int64_t ncache, int64_t r0
       } else {
         // this thread's ||bh|| over its rows, and the number of rows it sums (for s2)
         float ny2 = 0.f;
-        if (act)
-          for (int64_t li = l0 + rl; li < nrows; li += nrl) {
+        if (act) {  // eight independent sums: a single dependent chain costs a load latency per row
+          float e8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+          int li = (int)l0 + rl;
+          for (; li + 7 * nrl < (int)nrows; li += 8 * nrl)
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const float h = y2[li + u * nrl].x;
+              e8[u] = fmaf(h, h, e8[u]);
+            }
+          for (; li < (int)nrows; li += nrl) {
             const float h = y2[li].x;
-            ny2 = fmaf(h, h, ny2);
+            e8[0] = fmaf(h, h, e8[0]);
           }
+          ny2 = ((e8[0] + e8[1]) + (e8[2] + e8[3])) + ((e8[4] + e8[5]) + (e8[6] + e8[7]));
+        }
         const float sy = sqrtf(ny2) * kMargin;
         const int lk = 64 - __clzll((nrows - l0 + nrl - 1) / nrl + 1);  // 2^lk > rows per thread
         for (int64_t q0 = 0, it = 0; q0 < nq; q0 += cw, ++it) {
@@ -555,7 +565,7 @@ __device__ void ccolsum(const CArgs &a, const AT *As, int64_t ncache, int64_t r0
             seg4_off<true>(reinterpret_cast<const float4 *>(A) + r0 * ld4 + qc, (int)ld4, (int)max(l0, ncache),
                            (int)nrows, rl, nrl, y2, d);
           }
-          group_sync<NT>();
+          if (it > 0) group_sync<NT>();  // the previous chunk's sums are read (the first: the caller's barrier)
 #pragma unroll
           for (int c = 0; c < 4; ++c)  // hi - s1 and mid - s2 are exact (Sterbenz)
             red[c * NT + threadIdx.x] = make_float2(d[c].hi - s1[c], (d[c].mid - off_s2(s1[c], lk)) + d[c].lo);
