@@ -183,7 +183,8 @@ tucker_status launch_loss_grad(Ctx *c, const float *const *U, const float *G, do
   const int64_t I1 = c->dims[0], P1 = c->mode[0].P;
   const int R1 = c->ranks[0];
   const int chunks = (int)std::max<int64_t>(1, std::min<int64_t>(64, (I1 + 255) / 256));
-  if (!c->adj_e0) {
+  if (!c->adj_e0) {  // first call: buffers allocated in the order of s, ready for any stream after the sync
+    c->astream = s;
     TK_CUDA(dev_alloc(c, &c->adj_e0, (size_t)std::max<int64_t>(Z, 1)));
     TK_CUDA(dev_alloc(c, &c->adj_en, (size_t)std::max<int64_t>(Z, 1)));
     TK_CUDA(dev_alloc(c, &c->adj_Y, (size_t)ymax));
@@ -191,6 +192,8 @@ tucker_status launch_loss_grad(Ctx *c, const float *const *U, const float *G, do
     TK_CUDA(dev_alloc(c, &c->adj_Gn, (size_t)PR));
     TK_CUDA(dev_alloc(c, &c->adj_part, (size_t)kAdjRedBlocks));
     TK_CUDA(dev_alloc(c, &c->adj_gpart, (size_t)(64 * PR)));
+    TK_CUDA(cudaStreamSynchronize(s));
+    c->astream = 0;
   }
   // (1) Q = U_1 G_(1)
   adj_q_kernel<<<blocks_for(I1 * P1), 256, 0, s>>>(U[0], G, I1, R1, P1, c->adj_Q);

@@ -95,6 +95,7 @@ static int qrp_n_cols(const Ctx *c, int n) {
 static tucker_status init_impl(Ctx *c, const uint32_t *coords, const float *vals, const double *U0, uint64_t seed,
                                cudaStream_t s) {
   const int N = c->N;
+  c->astream = s;
   TK_CUDA(cudaGetDevice(&c->device));
   TK_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
   TK_CUDA(dev_alloc(c, &c->d_err, 4));
@@ -117,12 +118,9 @@ static tucker_status init_impl(Ctx *c, const uint32_t *coords, const float *vals
     dvals = stage_v;
   }
   tucker_status st = build_sorted_copies(c, dcoords, dvals, s);
-  if (stage_c) {
-    cudaStreamSynchronize(s);
-    c->allocs.erase(std::find(c->allocs.begin(), c->allocs.end(), (void *)stage_c));
-    c->allocs.erase(std::find(c->allocs.begin(), c->allocs.end(), (void *)stage_v));
-    cudaFree(stage_c);
-    cudaFree(stage_v);
+  if (stage_c) {  // freed in stream order, after the sorts that read them
+    dev_free(c, stage_c);
+    dev_free(c, stage_v);
   }
   if (st != TUCKER_OK) return st;
 
@@ -199,13 +197,12 @@ static tucker_status init_impl(Ctx *c, const uint32_t *coords, const float *vals
                        nullptr, &w, c->num_sms, s);
       if (st != TUCKER_OK) return st;
     }
-    TK_CUDA(cudaStreamSynchronize(s));
-    c->allocs.erase(std::find(c->allocs.begin(), c->allocs.end(), (void *)g));
-    cudaFree(g);
+    dev_free(c, g);
   }
   for (int m = 0; m < N; ++m) refresh_factor_copies(c, m, s);
   TK_CUDA(cudaGetLastError());
   TK_CUDA(cudaStreamSynchronize(s));
+  c->astream = 0;  // the caller may destroy s; later allocations name their own stream
   return TUCKER_OK;
 }
 
@@ -301,7 +298,8 @@ double tucker_norm2(const tucker_ctx *c) { return c ? c->c.norm2 : 0.0; }
 void tucker_free(tucker_ctx *c) {
   if (!c) return;
   cudaDeviceSynchronize();
-  for (void *p : c->c.allocs) cudaFree(p);
+  for (void *p : c->c.allocs) cudaFreeAsync(p, 0);  // back to the library's pool
+  cudaStreamSynchronize(0);
   for (cudaEvent_t e : c->c.ev)
     if (e) cudaEventDestroy(e);
   delete c;

@@ -134,6 +134,7 @@ struct Ctx {
   int n_ev = 0;
 
   std::vector<void *> allocs;  // every device allocation, freed by tucker_free
+  cudaStream_t astream = 0;    // the stream allocations and frees are ordered on (the current call's)
   std::string last_error;
 };
 
@@ -142,6 +143,7 @@ void count_launch();
 
 // ---- allocation (host-side failure injection for tests: TUCKER_FAIL_ALLOC_AT=k fails the k-th)
 cudaError_t dev_alloc(Ctx *c, void **p, size_t bytes);
+void dev_free(Ctx *c, void *p);  // one of c's allocations, in the order of c->astream
 template <typename T>
 cudaError_t dev_alloc(Ctx *c, T **p, size_t count) {
   return dev_alloc(c, reinterpret_cast<void **>(p), count * sizeof(T));
