@@ -195,26 +195,34 @@ constexpr int kRsWarps = kRsThreads / 32;
 constexpr int kRsPerWarp = 512;
 constexpr int kRsTile = kRsWarps * kRsPerWarp;
 
-__global__ void __launch_bounds__(kRsThreads) radix_hist_kernel(const uint32_t *key, const uint32_t *perm, int64_t n,
-                                                                int shift, uint32_t *hist) {
+// The keys of a sort are gathered once (key[perm[e]]) into a contiguous array and carried
+// with the permutation through the passes, so every pass reads both coalesced; only the
+// scatter writes go to data-dependent positions.
+__global__ void gather_keys_kernel(const uint32_t *key, const uint32_t *perm, int64_t n, uint32_t *out) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = __ldg(key + perm[e]);
+}
+
+__global__ void __launch_bounds__(kRsThreads) radix_hist_kernel(const uint32_t *k, int64_t n, int shift,
+                                                                uint32_t *hist) {
   __shared__ uint32_t h[256];
   h[threadIdx.x] = 0;
   __syncthreads();
   const int64_t base = (int64_t)blockIdx.x * kRsTile;
   for (int i = threadIdx.x; i < kRsTile; i += kRsThreads) {
     int64_t e = base + i;
-    if (e < n) {
-      uint32_t k = key[perm ? perm[e] : (uint32_t)e];
-      atomicAdd(&h[(k >> shift) & 255u], 1u);
-    }
+    if (e < n) atomicAdd(&h[(k[e] >> shift) & 255u], 1u);
   }
   __syncthreads();
   hist[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
 }
 
-__global__ void __launch_bounds__(kRsThreads) radix_scatter_kernel(const uint32_t *key, const uint32_t *perm_in,
-                                                                   uint32_t *perm_out, int64_t n, int shift,
-                                                                   const uint32_t *hist_off) {
+// One stable pass: element e (key kin[e], source pin[e], or e when pin is null) goes to
+// position hist_off[digit, block] + (rank among this block's earlier elements of its
+// digit); kout (skipped when null) receives the keys in the new order.
+__global__ void __launch_bounds__(kRsThreads) radix_scatter_kernel(const uint32_t *kin, const uint32_t *pin,
+                                                                   uint32_t *kout, uint32_t *pout, int64_t n,
+                                                                   int shift, const uint32_t *hist_off) {
   __shared__ uint32_t wh[kRsWarps][256];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   for (int i = tid; i < kRsWarps * 256; i += kRsThreads) wh[i / 256][i % 256] = 0;
@@ -222,10 +230,7 @@ __global__ void __launch_bounds__(kRsThreads) radix_scatter_kernel(const uint32_
   const int64_t wbase = (int64_t)blockIdx.x * kRsTile + (int64_t)w * kRsPerWarp;
   for (int st = 0; st < kRsPerWarp / 32; ++st) {
     int64_t e = wbase + st * 32 + lane;
-    if (e < n) {
-      uint32_t k = key[perm_in ? perm_in[e] : (uint32_t)e];
-      atomicAdd(&wh[w][(k >> shift) & 255u], 1u);
-    }
+    if (e < n) atomicAdd(&wh[w][(kin[e] >> shift) & 255u], 1u);
   }
   __syncthreads();
   {  // thread tid owns digit tid: running offset over the warps of this block
@@ -241,10 +246,11 @@ __global__ void __launch_bounds__(kRsThreads) radix_scatter_kernel(const uint32_
   for (int st = 0; st < kRsPerWarp / 32; ++st) {
     int64_t e = wbase + st * 32 + lane;
     bool valid = e < n;
-    uint32_t src = 0, d = 256u + lane;
+    uint32_t kk = 0, src = 0, d = 256u + lane;
     if (valid) {
-      src = perm_in ? perm_in[e] : (uint32_t)e;
-      d = (key[src] >> shift) & 255u;
+      kk = kin[e];
+      src = pin ? pin[e] : (uint32_t)e;
+      d = (kk >> shift) & 255u;
     }
     uint32_t peers = __match_any_sync(0xffffffffu, d);
     uint32_t rank = __popc(peers & lt);
@@ -252,7 +258,10 @@ __global__ void __launch_bounds__(kRsThreads) radix_scatter_kernel(const uint32_
     __syncwarp();
     if (valid && rank == 0) wh[w][d] += __popc(peers);
     __syncwarp();
-    if (valid) perm_out[pos] = src;
+    if (valid) {
+      pout[pos] = src;
+      if (kout) kout[pos] = kk;
+    }
   }
 }
 
@@ -264,19 +273,27 @@ static int bits_for(int64_t maxval) {
 
 // Stable sort of the permutation by key[perm[e]] (all bits of key < 2^bits).
 // On return *perm points at the sorted permutation (one of pa / pb), or stays
-// nullptr (identity) when no pass was needed.
+// nullptr (identity) when no pass was needed.  ka / kb hold the carried keys.
 static void radix_sort_perm(const uint32_t *key, int bits, int64_t n, uint32_t **perm, uint32_t *pa, uint32_t *pb,
-                            uint32_t *hist, uint32_t *tmp, cudaStream_t s) {
-  if (n <= 1) return;
+                            uint32_t *ka, uint32_t *kb, uint32_t *hist, uint32_t *tmp, cudaStream_t s) {
+  if (n <= 1 || bits <= 0) return;
   const int64_t nb = cdiv(n, kRsTile);
+  const uint32_t *kin = key;
+  if (*perm) {
+    gather_keys_kernel<<<(unsigned)std::min<int64_t>(cdiv(n, 256), 65535LL * 8), 256, 0, s>>>(key, *perm, n, ka);
+    ::tk::count_launch();
+    kin = ka;
+  }
   for (int shift = 0; shift < bits; shift += 8) {
     uint32_t *out = (*perm == pa) ? pb : pa;
-    radix_hist_kernel<<<(unsigned)nb, kRsThreads, 0, s>>>(key, *perm, n, shift, hist);
+    uint32_t *kout = shift + 8 < bits ? (kin == ka ? kb : ka) : nullptr;  // the last pass needs no keys
+    radix_hist_kernel<<<(unsigned)nb, kRsThreads, 0, s>>>(kin, n, shift, hist);
     ::tk::count_launch();
     exclusive_scan_u32(hist, hist, 256 * nb, tmp, s);
-    radix_scatter_kernel<<<(unsigned)nb, kRsThreads, 0, s>>>(key, *perm, out, n, shift, hist);
+    radix_scatter_kernel<<<(unsigned)nb, kRsThreads, 0, s>>>(kin, *perm, kout, out, n, shift, hist);
     ::tk::count_launch();
     *perm = out;
+    kin = kout;
   }
 }
 
@@ -612,9 +629,11 @@ tucker_status build_sorted_copies(Ctx *c, const uint32_t *coords_in, const float
   int64_t maxI = 1;
   for (int m = 0; m < N; ++m) maxI = std::max(maxI, c->dims[m]);
   const int64_t scan_n = std::max<int64_t>(std::max<int64_t>(256 * nb, nmax), maxI + 1);
-  uint32_t *pa, *pb, *hist, *stmp, *flag, *pos;
+  uint32_t *pa, *pb, *ka, *kb, *hist, *stmp, *flag, *pos;
   TK_TRY(tmp.get(&pa, nmax));
   TK_TRY(tmp.get(&pb, nmax));
+  TK_TRY(tmp.get(&ka, nmax));
+  TK_TRY(tmp.get(&kb, nmax));
   TK_TRY(tmp.get(&hist, 256 * nb));
   TK_TRY(tmp.get(&stmp, scan_tmp_elems(scan_n)));
   TK_TRY(tmp.get(&flag, std::max<int64_t>(nmax, maxI + 1)));
@@ -623,7 +642,7 @@ tucker_status build_sorted_copies(Ctx *c, const uint32_t *coords_in, const float
   // ---- full-key sort: LSD over modes N..1, each mode's digits low to high
   uint32_t *perm = nullptr;
   for (int m = N - 1; m >= 0; --m)
-    radix_sort_perm(coords_in + (int64_t)m * n_in, bits_for(c->dims[m] - 1), n_in, &perm, pa, pb, hist, stmp, s);
+    radix_sort_perm(coords_in + (int64_t)m * n_in, bits_for(c->dims[m] - 1), n_in, &perm, pa, pb, ka, kb, hist, stmp, s);
   TK_TRY(cudaGetLastError());
 
   // ---- coalesce duplicates
@@ -693,7 +712,7 @@ tucker_status build_sorted_copies(Ctx *c, const uint32_t *coords_in, const float
     }
     TK_TRY(dev_alloc(c, &mc.val, (size_t)std::max<int64_t>(Z, 1)));
     uint32_t *mperm = nullptr;  // mode 1: the lexicographic order is already sorted by i_1
-    if (n > 0) radix_sort_perm(c->coords + (int64_t)n * Z, bits_for(mc.I - 1), Z, &mperm, pa, pb, hist, stmp, s);
+    if (n > 0) radix_sort_perm(c->coords + (int64_t)n * Z, bits_for(mc.I - 1), Z, &mperm, pa, pb, ka, kb, hist, stmp, s);
     if (n > 0 && Z > 0) {
       TK_TRY(dev_alloc(c, &mc.src, (size_t)Z));
       if (mperm) {
@@ -769,8 +788,8 @@ tucker_status build_sorted_copies(Ctx *c, const uint32_t *coords_in, const float
     const bool alt = c->mode[b].other[0] == n && fnat[b] > 0 && (double)fnat[b] <= 0.8 * (double)fnat[n];
     uint32_t *perm = nullptr;
     if (alt) {  // stable sorts of the lexicographic list by i_b, then by i_n
-      radix_sort_perm(c->coords + (int64_t)b * Z, bits_for(c->dims[b] - 1), Z, &perm, pa, pb, hist, stmp, s);
-      radix_sort_perm(c->coords + (int64_t)n * Z, bits_for(mc.I - 1), Z, &perm, pa, pb, hist, stmp, s);
+      radix_sort_perm(c->coords + (int64_t)b * Z, bits_for(c->dims[b] - 1), Z, &perm, pa, pb, ka, kb, hist, stmp, s);
+      radix_sort_perm(c->coords + (int64_t)n * Z, bits_for(mc.I - 1), Z, &perm, pa, pb, ka, kb, hist, stmp, s);
       if (!mc.src) TK_TRY(dev_alloc(c, &mc.src, (size_t)Z));
       if (perm) {
         TK_TRY(cudaMemcpyAsync(mc.src, perm, sizeof(uint32_t) * (size_t)Z, cudaMemcpyDeviceToDevice, s));
