@@ -188,6 +188,32 @@ __device__ __forceinline__ float2 df2_add(float2 a, float2 b) {
   return make_float2(x.hi, x.lo);
 }
 
+// t -= (v.x + v.y) (m.x + m.y): the product of the high parts exactly (FMA residual), the
+// cross terms by FMA, the low-low term dropped (2^-48 of the product); TwoSum of the high parts
+__device__ __forceinline__ void df_sub_prod(DF &t, float2 v, float2 m) {
+  const float p = v.x * m.x;
+  float e = fmaf(v.x, m.x, -p);
+  e = fmaf(v.x, m.y, e);
+  e = fmaf(v.y, m.x, e);
+  const float s = t.hi - p;
+  const float bp = s - t.hi;
+  const float err = (t.hi - (s - bp)) - (p + bp);
+  t.hi = s;
+  t.lo += err - e;
+}
+
+// FP32 -> FP64 without the FP64 pipe: the same sign, the exponent rebiased (+896), the
+// mantissa shifted up 29 bits; exact for normal numbers (zero, subnormals, inf and NaN
+// take the conversion instruction)
+__device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned e = (b >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) return (double)f;
+  const unsigned long long d = ((unsigned long long)(b & 0x80000000u) << 32) |
+                               ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(b & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)d);
+}
+
 template <typename PT>
 struct Part;
 template <>
@@ -834,6 +860,7 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
       double *vr = Vs + li * kp;
       if (i < j) {
         vr[j] = 0.0;
+        if constexpr (sizeof(AT) == 4) reinterpret_cast<float2 *>(a.Q)[i * a.ldq + j] = make_float2(0.f, 0.f);
         continue;
       }
       double y = li < ncache ? (double)As[li * n + c0] : (double)__ldg(A + i * a.lda + c0);
@@ -842,7 +869,9 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
       s2 = fma(y, y, s2);
       if constexpr (sizeof(AT) == 4) {
         const float h = (float)y;
-        static_cast<float2 *>(ys)[li] = make_float2(h, (float)(y - (double)h));
+        const float2 yp = make_float2(h, (float)(y - (double)h));
+        static_cast<float2 *>(ys)[li] = yp;
+        reinterpret_cast<float2 *>(a.Q)[i * a.ldq + j] = yp;  // V[i, j] as a pair, for the Q formation
       } else {
         static_cast<double *>(ys)[li] = y;
       }
@@ -916,7 +945,10 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
       s_sc[1] = tau;
       s_sc[2] = v0 - x0;
       Vt[j * k + j] = v0;
-      if (owner) Vs[(j - r0) * kp + j] = v0;
+      if (owner) {
+        Vs[(j - r0) * kp + j] = v0;
+        if constexpr (sizeof(AT) == 4) reinterpret_cast<float2 *>(a.Q)[(int64_t)j * a.ldq + j] = df2_of(v0);
+      }
       if (blockIdx.x == 0) {
         if (a.rdiag) a.rdiag[j] = beta;
         if (a.piv) a.piv[j] = c0;
@@ -1035,14 +1067,43 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
     Ms[q] = t;
   }
   __syncthreads();
-  for (int64_t idx = tid; idx < nrows * k; idx += kCT) {
-    const int64_t li = idx / k, i = r0 + li;
-    const int cc = (int)(idx % k);
-    double t = (i == cc) ? 1.0 : 0.0;
-    const int lmax = (int)min((int64_t)k - 1, i);
-    const double *vr = Vs + li * kp;
-    for (int l = 0; l <= lmax; ++l) t = fma(-vr[l], Ms[l * k + cc], t);
-    a.Q[i * a.ldq + cc] = t;
+  if constexpr (sizeof(AT) == 4) {
+    // FP32 A: V's entries were kept as double-float pairs in Q's slots during the steps;
+    // they replace the FP64 copy in shared memory (no longer needed), M is split in place,
+    // and each entry of Q is a double-float sum on the FP32 pipe (about 2^-47 relative),
+    // converted to FP64 with one FP64 addition: 16 FP64 operations per row instead of
+    // k^2 = 256 FMAs, on a pipe that issues one warp instruction per 16 cycles per SM.
+    float2 *Vsf = reinterpret_cast<float2 *>(Vs);
+    float2 *Mf = reinterpret_cast<float2 *>(Ms);
+    const float2 *Qf = reinterpret_cast<const float2 *>(a.Q);
+    for (int64_t idx = tid; idx < nrows * k; idx += kCT) {
+      const int64_t li = idx / k;
+      const int l = (int)(idx % k);
+      Vsf[li * kp + l] = Qf[(r0 + li) * a.ldq + l];
+    }
+    for (int q = tid; q < k * k; q += kCT) Mf[q] = df2_of(Ms[q]);  // each slot read, then rewritten, by one thread
+    __syncthreads();
+    for (int64_t idx = tid; idx < nrows * k; idx += kCT) {
+      const int64_t li = idx / k, i = r0 + li;
+      const int cc = (int)(idx % k);
+      DF t;
+      t.hi = (i == cc) ? 1.f : 0.f;
+      t.lo = 0.f;
+      const int lmax = (int)min((int64_t)k - 1, i);
+      const float2 *vr = Vsf + li * kp;
+      for (int l = 0; l <= lmax; ++l) df_sub_prod(t, vr[l], Mf[l * k + cc]);
+      a.Q[i * a.ldq + cc] = f2d_exact(t.hi) + f2d_exact(t.lo);
+    }
+  } else {
+    for (int64_t idx = tid; idx < nrows * k; idx += kCT) {
+      const int64_t li = idx / k, i = r0 + li;
+      const int cc = (int)(idx % k);
+      double t = (i == cc) ? 1.0 : 0.0;
+      const int lmax = (int)min((int64_t)k - 1, i);
+      const double *vr = Vs + li * kp;
+      for (int l = 0; l <= lmax; ++l) t = fma(-vr[l], Ms[l * k + cc], t);
+      a.Q[i * a.ldq + cc] = t;
+    }
   }
   cl.sync();  // no block leaves while a peer may still read its shared memory
 }
