@@ -10,7 +10,7 @@
  * Every routine is a plain, slow restatement of the paper's definitions in double
  * precision: loops in the order the paper states them, no blocking, no fusion.
  *
- * Conventions (readings of the paper, listed with their reasons in the design notes):
+ * Conventions (readings of the paper where it leaves the layout open):
  *   - indices are 0-based; tensors are given in COO form, coords[m*nnz + z] = i_m(z)
  *     (Section III-A, Table I);
  *   - factor U_m is I_m x R_m, row-major (Section III, Tucker model);
