@@ -41,3 +41,26 @@ def test_status_strings_without_a_gpu():
     lib.tucker_status_str.restype = ctypes.c_char_p
     assert lib.tucker_status_str(0) == b"ok"
     assert lib.tucker_status_str(2) == b"rank out of range"
+
+
+def test_device_entry_points_refuse_host_tensors():
+    """No host fallback: the device entry points reject CPU tensors and other dtypes
+    before any call into the library."""
+    import pytest
+    torch = pytest.importorskip("torch")
+    from paper_2010_10638_gb300 import build, tucker
+    build.build()
+    tucker.load()
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        tucker.qrp_leading(torch.zeros(8, 4, dtype=torch.float64), 2)
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        tucker.qrp_leading_noalloc(torch.zeros(8, 4, dtype=torch.float32), 2)
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without the built library the binding raises instead of computing anything."""
+    import pytest
+    from paper_2010_10638_gb300 import tucker
+    monkeypatch.setattr(tucker, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        tucker.load(str(tmp_path / "libtucker.so"))
