@@ -1076,10 +1076,19 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
     float2 *Vsf = reinterpret_cast<float2 *>(Vs);
     float2 *Mf = reinterpret_cast<float2 *>(Ms);
     const float2 *Qf = reinterpret_cast<const float2 *>(a.Q);
-    for (int64_t idx = tid; idx < nrows * k; idx += kCT) {
-      const int64_t li = idx / k;
-      const int l = (int)(idx % k);
-      Vsf[li * kp + l] = Qf[(r0 + li) * a.ldq + l];
+    const int64_t tot = nrows * k;
+    for (int64_t b0 = tid; b0 < tot; b0 += 8 * kCT) {  // eight loads in flight per thread, then the stores
+      float2 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int64_t idx = b0 + (int64_t)u * kCT;
+        if (idx < tot) v[u] = Qf[(r0 + idx / k) * a.ldq + idx % k];
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int64_t idx = b0 + (int64_t)u * kCT;
+        if (idx < tot) Vsf[(idx / k) * kp + idx % k] = v[u];
+      }
     }
     for (int q = tid; q < k * k; q += kCT) Mf[q] = df2_of(Ms[q]);  // each slot read, then rewritten, by one thread
     __syncthreads();
