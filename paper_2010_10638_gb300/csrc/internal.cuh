@@ -54,6 +54,8 @@ struct ModeCopy {
   uint32_t *fptr = nullptr;            // [F+1] first sorted position of each fiber
   uint32_t *fmid = nullptr;            // [F] index of the first remaining mode of each fiber
   uint32_t *fsptr = nullptr;           // [S+1] first fiber of each non-empty slice
+  uint32_t *fbits = nullptr;           // [Z/32 + 3] bit e: sorted position e starts a fiber (zero padded)
+  uint32_t *unit_f0 = nullptr;         // [n_units] fiber containing the first position of each nonzero unit
   int fchunk = 0;
   uint32_t *funit_e0 = nullptr, *funit_k0 = nullptr;
   int32_t *funit_slot = nullptr;
@@ -167,6 +169,9 @@ tucker_status launch_ttmc_ex(Ctx *c, int mode, float *Y, const float *val, const
 
 // ---- K-c: QRP (qrp.cu)
 size_t qrp_work_bytes(int64_t m, int64_t n, int k, int nb);
+// standalone QRP calls keep their error word in the first bytes of their scratch
+constexpr size_t kQrpErrWordBytes = 256;
+tucker_status qrp_read_err_word(uint32_t *word, cudaStream_t s);
 void qrp_bind_work(QrpWork *w, void *base, int64_t m, int64_t n, int k, int nb);
 // A is m x n (row stride lda) of type float or double; writes Q (m x k, row stride ldq),
 // piv (int64, may be null), rdiag (may be null).

@@ -443,6 +443,24 @@ __global__ void fiber_write_kernel(int64_t n, const uint32_t *cut, const uint32_
   }
 }
 
+// bit e of words[e / 32]: position e starts a fiber (one warp per 32 positions)
+__global__ void fiber_bits_kernel(int64_t n, const uint32_t *cut, uint32_t *words) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e - lane < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned b = __ballot_sync(0xffffffffu, e < n && cut[e] != 0u);
+    if (lane == 0) words[e >> 5] = b;
+  }
+}
+
+// fiber containing the first position of each nonzero work unit
+__global__ void unit_fiber_kernel(int64_t n_units, const uint32_t *unit_e0, const uint32_t *cut, const uint32_t *cpos,
+                                  uint32_t *unit_f0) {
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n_units; u += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t e = unit_e0[u];
+    unit_f0[u] = cpos[e] + cut[e] - 1u;
+  }
+}
+
 __global__ void fiber_slices_kernel(int64_t S, const uint32_t *sptr, const uint32_t *cpos, uint32_t *fsptr,
                                     int64_t F) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < S; k += (int64_t)gridDim.x * blockDim.x) {
@@ -838,6 +856,18 @@ tucker_status build_sorted_copies(Ctx *c, const uint32_t *coords_in, const float
       ::tk::count_launch();
       fiber_slices_kernel<<<grid_for(mc.S), 256, 0, s>>>(mc.S, mc.sptr, fcpos, mc.fsptr, F);
       ::tk::count_launch();
+      {  // fiber starts as a bit mask over the sorted positions, three zero words past the end
+        const int64_t nw = (Z + 31) / 32 + 3;
+        TK_TRY(dev_alloc(c, &mc.fbits, (size_t)nw));
+        TK_TRY(cudaMemsetAsync(mc.fbits, 0, sizeof(uint32_t) * (size_t)nw, s));
+        fiber_bits_kernel<<<grid_for((Z + 31) / 32 * 32), 256, 0, s>>>(Z, fcut, mc.fbits);
+        ::tk::count_launch();
+        TK_TRY(dev_alloc(c, &mc.unit_f0, (size_t)std::max<int64_t>(mc.n_units, 1)));
+        if (mc.n_units > 0) {
+          unit_fiber_kernel<<<grid_for(mc.n_units), 256, 0, s>>>(mc.n_units, mc.unit_e0, fcut, fcpos, mc.unit_f0);
+          ::tk::count_launch();
+        }
+      }
       TK_TRY(cudaGetLastError());
       // a fiber unit spans about as many nonzeros as a nonzero unit (a fiber costs its
       // nonzeros plus one rank-1 update), in multiples of 32 fibers

@@ -556,6 +556,346 @@ __global__ void __launch_bounds__(kTtmcWarps * 32) ttmc_fibsum_kernel(const Ttmc
   }
 }
 
+// ============================================================================ fused fiber form
+// Both levels of the fiber form in one kernel, the fiber sums never leaving the chip.
+// One warp per nonzero work unit [z0, z1) (the nonzero form's units: runs of whole slices of
+// about `chunk` nonzeros, or one piece of a longer slice).  A fiber cut by a piece boundary
+// is a fiber of each piece: both pieces belong to one long slice, whose partial rows the
+// fixup kernel adds, and the fiber's rank-1 update is linear in its sum.
+//   Level 1, per window of kWin consecutive nonzeros: lane (block pb, quad q) adds
+//     x_z U_s(i_s(z), 4q..4q+3) over the PB positions of its block in order (U_s: the
+//     factor of the summed mode; rows gathered coalesced, QL lanes per row), closing the
+//     fibers that start and end inside the block; the pieces before a block's first fiber
+//     start and after its last are joined across blocks by a shuffle scan of the maps
+//     "A -> A + lead" (no start) and "A -> trail" (a start), applied to the fiber carried
+//     over from the previous window.  Fiber starts come from a per-position bit mask.
+//     Finished t_f go to a per-warp ring in shared memory (kRing rows).
+//   Level 2, whenever 32 finished fibers wait (and at the unit's end): the pipelined
+//     kernel's tile over fibers: rows U_m(fmid(f)) of the middle mode gathered, rows t_f
+//     from the ring, a TA x TB block of the slice row per lane, NG groups merged by
+//     shuffles where a slice closes, rows written to Y (or to a partial-row slot).
+// MIDA: the middle mode is the first remaining mode (Y column = r_mid * RS + r_sum);
+// otherwise it is the last one (Y column = r_sum * RM + r_mid).  Fixed orders: Y is
+// reproducible bit for bit.
+constexpr int kFibWarps = 4;
+
+struct FiberParams {
+  const float *val;      // [Z] values, in the copy's order
+  const uint32_t *isum;  // [Z] index of the summed mode
+  const void *Usum;      // its factor (float or bf16), I x RS
+  const void *Umid;      // factor of the middle mode, I x RM
+  const uint32_t *fptr;  // [F+1]
+  const uint32_t *fmid;  // [F]
+  const uint32_t *fbits; // fiber starts, one bit per position (zero padded)
+  const uint32_t *fsptr; // [S+1] first fiber of each non-empty slice
+  const uint32_t *sid;   // [S]
+  uint32_t S, F, Z;
+  const uint32_t *unit_e0;  // [n_units] first position of each unit
+  const uint32_t *unit_f0;  // [n_units] fiber containing it
+  const uint32_t *unit_k0;  // [n_units] slice containing it
+  const int32_t *unit_slot;
+  int64_t n_units;
+  float *Y;
+  float *carry;
+  int64_t P;
+};
+
+template <typename FT>
+__device__ __forceinline__ float4 row4(const FT *U, uint32_t r, int R, int c) {
+  return Ld<FT>::v4(U + (size_t)r * R, c);
+}
+
+constexpr int kWinDefault = 64;  // nonzeros per level-1 window
+
+// 64 bits of the start mask beginning at position z
+__device__ __forceinline__ uint64_t start_bits64(const uint32_t *__restrict__ fbits, uint32_t z) {
+  const uint32_t w = z >> 5, sh = z & 31u;
+  const uint32_t a = __ldg(fbits + w), b = __ldg(fbits + w + 1), c = __ldg(fbits + w + 2);
+  const uint32_t lo = __funnelshift_r(a, b, sh), hi = __funnelshift_r(b, c, sh);
+  return ((uint64_t)hi << 32) | lo;
+}
+
+template <int RM, int RS, int TA, int TB, bool MIDA, typename FT, int kWin = 64, int MINB = 1>
+__global__ void __launch_bounds__(kFibWarps * 32, MINB) ttmc_fiber_kernel(const FiberParams p) {
+  constexpr int kRing = 2 * kWin;  // ring rows: < 32 waiting + at most kWin + 1 finished per window
+  constexpr int PL = MIDA ? RM : RS, RB = MIDA ? RS : RM;
+  constexpr int G = (PL / TA) * (RB / TB);
+  constexpr int NG = 32 / G;
+  static_assert(G * NG == 32, "group size must divide the warp");
+  static_assert(RM % 4 == 0 && RS % 4 == 0, "16-byte row pieces");
+  constexpr int QL = RS / 4;          // lanes per summed-mode row
+  constexpr int PG = 32 / QL;         // position blocks per window
+  constexpr int PB = kWin / PG;       // positions per block
+  static_assert(QL * PG == 32 && PB * PG == kWin && PG <= 32, "window layout");
+  constexpr int WARP_FLOATS = kRing * RS + 32 * RM + 2 * (kWin + 32);
+  // window entry of position t, one spare entry per block so that the blocks' reads fall in
+  // distinct banks
+  auto xsi = [](int t) { return t + t / PB; };
+  extern __shared__ float4 smem_f4[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float *ring = reinterpret_cast<float *>(smem_f4) + (size_t)w * WARP_FLOATS;
+  float *stage = ring + kRing * RS;                                 // 32 gathered middle-mode rows
+  uint2 *xs = reinterpret_cast<uint2 *>(stage + 32 * RM);           // window values and indices
+  float4 *ring4 = reinterpret_cast<float4 *>(ring);
+  const int64_t u = (int64_t)blockIdx.x * kFibWarps + w;
+  if (u >= p.n_units) return;
+  const FT *US = static_cast<const FT *>(p.Usum);
+  const FT *UM = static_cast<const FT *>(p.Umid);
+  const uint32_t f0 = __ldg(p.unit_f0 + u);
+  const uint32_t z0 = __ldg(p.unit_e0 + u);
+  const uint32_t z1 = (u + 1 < p.n_units) ? __ldg(p.unit_e0 + u + 1) : p.Z;
+  // one past the unit's last fiber (the next unit may begin inside it)
+  const uint32_t f1 = (u + 1 < p.n_units)
+                          ? __ldg(p.unit_f0 + u + 1) + (((__ldg(p.fbits + (z1 >> 5)) >> (z1 & 31u)) & 1u) ? 0u : 1u)
+                          : p.F;
+  const int slot = __ldg(p.unit_slot + u);
+  const int q = lane % QL, pb = lane / QL, P0 = pb * PB;
+  const int g = lane / G, j = lane % G;
+  const int ra0 = (j / (RB / TB)) * TA, rb0 = (j % (RB / TB)) * TB;
+  auto ring_slot = [&](uint32_t f) { return (int)((f - f0) & (uint32_t)(kRing - 1)); };
+
+  float acc[TA][TB];
+#pragma unroll
+  for (int a = 0; a < TA; ++a)
+#pragma unroll
+    for (int b = 0; b < TB; ++b) acc[a][b] = 0.f;
+  uint32_t kb2 = __ldg(p.unit_k0 + u);  // slice of fiber fdone
+  uint32_t fdone = f0;                  // level 2 has consumed fibers [f0, fdone)
+  uint32_t fcur = f0;                   // fiber open at the end of the last window
+  float4 carry = make_float4(0.f, 0.f, 0.f, 0.f);
+
+  // level 2 over the finished fibers [fdone, fdone + nt)
+  auto level2 = [&](int nt) {
+    const uint32_t e = fdone;
+    const uint32_t bound = (kb2 + 1u + lane <= p.S) ? __ldg(p.fsptr + kb2 + 1u + lane) : 0xffffffffu;
+    const uint32_t fm = (lane < nt) ? __ldg(p.fmid + e + lane) : 0u;
+    const uint32_t qd = bound - e;
+    uint32_t starts = __reduce_or_sync(kFull, qd < 32u ? (1u << qd) : 0u);
+    starts &= (nt >= 32) ? kFull : ((1u << nt) - 1u);
+    const uint32_t kp = kb2 + __popc(starts & ((2u << lane) - 1u));
+    const bool end_is_start = __any_sync(kFull, qd == (uint32_t)nt);
+    const uint32_t kb_next = kb2 + __popc(__ballot_sync(kFull, qd <= (uint32_t)nt));
+#pragma unroll
+    for (int it = lane; it < 32 * (RM / 4); it += 32) {
+      const int tt = it / (RM / 4), c = (it % (RM / 4)) * 4;
+      const uint32_t r = __shfl_sync(kFull, fm, tt);
+      if (tt < nt) *reinterpret_cast<float4 *>(stage + tt * RM + c) = row4(UM, r, RM, c);
+    }
+    __syncwarp();
+    const int rbase = ring_slot(e);
+    auto arow = [&](int r) -> const float * {
+      if constexpr (MIDA) return stage + r * RM;
+      else return ring + ((rbase + r) & (kRing - 1)) * RS;
+    };
+    auto brow = [&](int r) -> const float * {
+      if constexpr (MIDA) return ring + ((rbase + r) & (kRing - 1)) * RS;
+      else return stage + r * RM;
+    };
+    uint32_t segs = starts | 1u;
+    while (segs) {
+      const int p0 = __ffs(segs) - 1;
+      segs &= segs - 1u;
+      const int p1 = segs ? (__ffs(segs) - 1) : nt;
+      int qq = p0 + g;
+      auto step = [&](int r) {
+        float av[TA], bv[TB];
+        lds<TA>(arow(r) + ra0, av);
+        lds<TB>(brow(r) + rb0, bv);
+#pragma unroll
+        for (int a = 0; a < TA; ++a)
+#pragma unroll
+          for (int b = 0; b < TB; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+      };
+      for (; qq + NG < p1; qq += 2 * NG) {
+        step(qq);
+        step(qq + NG);
+      }
+      if (qq < p1) step(qq);
+      const bool flush = (p1 < nt) || end_is_start || (e + (uint32_t)nt == f1);
+      if (flush) {
+#pragma unroll
+        for (int o = G; o < 32; o <<= 1)
+#pragma unroll
+          for (int a = 0; a < TA; ++a)
+#pragma unroll
+            for (int b = 0; b < TB; ++b) acc[a][b] += __shfl_xor_sync(kFull, acc[a][b], o);
+        const uint32_t kseg = __shfl_sync(kFull, kp, p0);
+        if (g == 0) {
+          float *dst = (slot >= 0) ? p.carry + (size_t)slot * p.P : p.Y + (size_t)__ldg(p.sid + kseg) * p.P;
+#pragma unroll
+          for (int a = 0; a < TA; ++a) {
+            float *d = dst + (size_t)(ra0 + a) * RB + rb0;
+#pragma unroll
+            for (int b = 0; b < TB; b += 4)
+              *reinterpret_cast<float4 *>(d + b) = make_float4(acc[a][b], acc[a][b + 1], acc[a][b + 2], acc[a][b + 3]);
+          }
+        }
+#pragma unroll
+        for (int a = 0; a < TA; ++a)
+#pragma unroll
+          for (int b = 0; b < TB; ++b) acc[a][b] = 0.f;
+      }
+    }
+    __syncwarp();
+    kb2 = kb_next;
+    fdone += (uint32_t)nt;
+  };
+
+  // level 1: window loads one window ahead
+  float xr[kWin / 32];
+  uint32_t ir[kWin / 32];
+#pragma unroll
+  for (int jj = 0; jj < kWin / 32; ++jj) {
+    const uint32_t pos = z0 + 32u * jj + lane;
+    xr[jj] = (pos < z1) ? __ldg(p.val + pos) : 0.f;
+    ir[jj] = (pos < z1) ? __ldg(p.isum + pos) : 0u;
+  }
+  for (uint32_t z = z0; z < z1; z += kWin) {
+    const int nt = (int)min((uint32_t)kWin, z1 - z);
+#pragma unroll
+    for (int jj = 0; jj < kWin / 32; ++jj) xs[xsi(32 * jj + lane)] = make_uint2(__float_as_uint(xr[jj]), ir[jj]);
+    uint64_t starts = start_bits64(p.fbits, z);
+    starts &= (nt >= 64) ? ~0ull : ((1ull << nt) - 1ull);
+    if (z != z0 && (starts & 1ull)) {  // the fiber carried in ended at z - 1
+      if (pb == 0) ring4[ring_slot(fcur) * QL + q] = carry;
+      ++fcur;
+      carry = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    starts &= ~1ull;
+#pragma unroll
+    for (int jj = 0; jj < kWin / 32; ++jj) {  // next window
+      const uint32_t pos = z + kWin + 32u * jj + lane;
+      xr[jj] = (pos < z1) ? __ldg(p.val + pos) : 0.f;
+      ir[jj] = (pos < z1) ? __ldg(p.isum + pos) : 0u;
+    }
+    __syncwarp();
+    float xv[PB];
+    float4 r[PB];
+#pragma unroll
+    for (int i = 0; i < PB; ++i) {
+      const uint2 e2 = xs[xsi(P0 + i)];
+      xv[i] = __uint_as_float(e2.x);
+      r[i] = (P0 + i < nt) ? row4(US, e2.y, RS, 4 * q) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    auto fiber_of = [&](int s) { return fcur + (uint32_t)__popcll(starts & ((2ull << s) - 1ull)); };
+    // local pass: lead piece, fibers inside the block, trail piece
+    float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f), lead = a4;
+    bool seen = false;
+#pragma unroll
+    for (int i = 0; i < PB; ++i) {
+      if ((starts >> (P0 + i)) & 1ull) {  // the fiber at P0 + i - 1 ends
+        if (seen)
+          ring4[ring_slot(fiber_of(P0 + i - 1)) * QL + q] = a4;
+        else
+          lead = a4;
+        seen = true;
+        a4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      a4.x = fmaf(xv[i], r[i].x, a4.x);
+      a4.y = fmaf(xv[i], r[i].y, a4.y);
+      a4.z = fmaf(xv[i], r[i].z, a4.z);
+      a4.w = fmaf(xv[i], r[i].w, a4.w);
+    }
+    if (!seen) lead = a4;
+    // block map: A -> (seen ? 0 : A) + (seen ? trail : lead); inclusive scan over blocks
+    bool cz = seen;
+    float4 cb = seen ? a4 : lead;
+#pragma unroll
+    for (int d = 1; d < PG; d <<= 1) {
+      const bool ez = __shfl_up_sync(kFull, (int)cz, d * QL) != 0;
+      float4 eb;
+      eb.x = __shfl_up_sync(kFull, cb.x, d * QL);
+      eb.y = __shfl_up_sync(kFull, cb.y, d * QL);
+      eb.z = __shfl_up_sync(kFull, cb.z, d * QL);
+      eb.w = __shfl_up_sync(kFull, cb.w, d * QL);
+      if (pb >= d && !cz) {
+        cz = ez;
+        cb.x = eb.x + cb.x;
+        cb.y = eb.y + cb.y;
+        cb.z = eb.z + cb.z;
+        cb.w = eb.w + cb.w;
+      }
+    }
+    // open fiber entering this block = (composition of the blocks before it)(carry)
+    const bool pz = __shfl_up_sync(kFull, (int)cz, QL) != 0;
+    float4 pbv;
+    pbv.x = __shfl_up_sync(kFull, cb.x, QL);
+    pbv.y = __shfl_up_sync(kFull, cb.y, QL);
+    pbv.z = __shfl_up_sync(kFull, cb.z, QL);
+    pbv.w = __shfl_up_sync(kFull, cb.w, QL);
+    float4 open = carry;
+    if (pb > 0) {
+      if (pz) {
+        open = pbv;
+      } else {
+        open.x = carry.x + pbv.x;
+        open.y = carry.y + pbv.y;
+        open.z = carry.z + pbv.z;
+        open.w = carry.w + pbv.w;
+      }
+    }
+    if (seen) {  // the open fiber ends at this block's first start
+      const uint64_t bm = ((PB >= 64) ? ~0ull : (((1ull << PB) - 1ull) << P0));
+      const int s0 = __ffsll((long long)(starts & bm)) - 1;
+      ring4[ring_slot(fiber_of(s0 - 1)) * QL + q] =
+          make_float4(open.x + lead.x, open.y + lead.y, open.z + lead.z, open.w + lead.w);
+    }
+    // the fiber open at the end of the window: the last block's composition applied to carry
+    const int last = PG - 1;
+    const bool lz = __shfl_sync(kFull, (int)cz, last * QL + q) != 0;
+    float4 fin;
+    fin.x = __shfl_sync(kFull, cb.x, last * QL + q);
+    fin.y = __shfl_sync(kFull, cb.y, last * QL + q);
+    fin.z = __shfl_sync(kFull, cb.z, last * QL + q);
+    fin.w = __shfl_sync(kFull, cb.w, last * QL + q);
+    if (!lz) {
+      fin.x = carry.x + fin.x;
+      fin.y = carry.y + fin.y;
+      fin.z = carry.z + fin.z;
+      fin.w = carry.w + fin.w;
+    }
+    carry = fin;
+    fcur += (uint32_t)__popcll(starts);
+    const bool unit_end = (z + (uint32_t)nt == z1);
+    if (unit_end) {  // the last fiber of the unit ends here
+      if (pb == 0) ring4[ring_slot(fcur) * QL + q] = carry;
+      ++fcur;
+    }
+    __syncwarp();
+    while (fcur - fdone >= 32u) level2(32);
+    if (unit_end && fcur > fdone) level2((int)(fcur - fdone));
+  }
+}
+
+template <int RM, int RS, int TA, int TB, bool MIDA, typename FT, int kWin = kWinDefault, int MINB = 4>
+static cudaError_t run_fiber(const FiberParams &p, cudaStream_t s) {
+  const size_t smem = (size_t)kFibWarps * (2 * kWin * RS + 32 * RM + 2 * (kWin + 32)) * sizeof(float);
+  auto kern = ttmc_fiber_kernel<RM, RS, TA, TB, MIDA, FT, kWin, MINB>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const unsigned blocks = (unsigned)((p.n_units + kFibWarps - 1) / kFibWarps);
+  kern<<<blocks, kFibWarps * 32, smem, s>>>(p);
+  ::tk::count_launch();
+  return cudaGetLastError();
+}
+
+// Fused fiber form for order-3 shapes (middle rank RM, summed rank RS).
+template <typename FT>
+static bool dispatch_fiber(const FiberParams &p, int RM, int RS, bool mida, cudaStream_t s, cudaError_t *err) {
+#define TK_FIB(RM_, RS_, TA_, TB_)                                                                        \
+  if (RM == RM_ && RS == RS_) {                                                                           \
+    *err = mida ? run_fiber<RM_, RS_, TA_, TB_, true, FT>(p, s) : run_fiber<RM_, RS_, TA_, TB_, false, FT>(p, s); \
+    return true;                                                                                          \
+  }
+  TK_FIB(16, 16, 4, 4)
+  TK_FIB(8, 8, 2, 4)
+  TK_FIB(32, 32, 8, 4)
+  TK_FIB(16, 8, 4, 4)
+  TK_FIB(8, 16, 4, 4)
+#undef TK_FIB
+  return false;
+}
+
 __global__ void fill_iota_ones_kernel(uint32_t *iota, float *ones, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     iota[i] = (uint32_t)i;
@@ -1264,6 +1604,16 @@ static bool dispatch_fast(const TtmcParams &p, cudaStream_t s, cudaError_t *err)
   return false;
 }
 
+// TUCKER_TTMC_FUSED=1 selects the fused fiber kernel instead of the two-pass fiber form.
+// Measured on the 20M-nonzero skewed workload it ran at best level with the two passes
+// (0.55 / 0.42 ms against 0.42 / 0.435 ms on its two fiber modes): both levels wait on
+// factor-row gathers, and holding the fiber ring and both levels' registers leaves fewer
+// resident warps to hide them.  It is kept as an opt-in form: it moves no t_f through HBM.
+static bool fused_fibers() {
+  const char *e = std::getenv("TUCKER_TTMC_FUSED");
+  return e && e[0] == '1';
+}
+
 static tucker_status ttmc_impl(Ctx *c, int mode, float *Y, const float *val, const float *const *Uf,
                                cudaStream_t s) {
   const ModeCopy &mc = c->mode[mode];
@@ -1289,7 +1639,48 @@ static tucker_status ttmc_impl(Ctx *c, int mode, float *Y, const float *val, con
   p.Y = Y;
   p.carry = c->carry;
   p.P = mc.P;
-  // FP32 factors with a fiber level: fiber sums, then the pipelined update over fibers
+  // A fiber level, opt-in fused kernel (fiber sums kept on chip), FP32 or BF16 factors
+  if (!(c->flags & (TUCKER_F_TF32X3 | TUCKER_F_UNPIPELINED)) && mc.fib && mc.n_units > 0 && mc.unit_f0 &&
+      p.nother == 2 && fused_fibers()) {
+    const int ft = mc.fmid_t;
+    FiberParams f{};
+    f.val = p.val;
+    f.isum = mc.idx[1 - ft];
+    f.Usum = p.U[1 - ft];
+    f.Umid = p.U[ft];
+    f.fptr = mc.fptr;
+    f.fmid = mc.fmid;
+    f.fbits = mc.fbits;
+    f.fsptr = mc.fsptr;
+    f.sid = mc.sid;
+    f.S = (uint32_t)mc.S;
+    f.F = (uint32_t)mc.F;
+    f.Z = (uint32_t)c->nnz;
+    f.unit_e0 = mc.unit_e0;
+    f.unit_f0 = mc.unit_f0;
+    f.unit_k0 = mc.unit_k0;
+    f.unit_slot = mc.unit_slot;
+    f.n_units = mc.n_units;
+    f.Y = Y;
+    f.carry = c->carry;
+    f.P = mc.P;
+    cudaError_t err = cudaSuccess;
+    const bool done = bf16 ? dispatch_fiber<__nv_bfloat16>(f, p.R[ft], p.R[1 - ft], ft == 0, s, &err)
+                           : dispatch_fiber<float>(f, p.R[ft], p.R[1 - ft], ft == 0, s, &err);
+    if (done) {
+      TK_CUDA(err);
+      if (mc.n_long > 0) launch_fixup(mc.long_k, mc.long_u0, mc.long_np, mc.n_long, mc.sid, c->carry, Y, mc.P, s);
+      if (mc.n_empty > 0) {
+        ttmc_zero_rows_kernel<<<(unsigned)std::min<int64_t>(mc.n_empty, 65535), 256, 0, s>>>(mc.empty, mc.n_empty,
+                                                                                            Y, mc.P);
+        ::tk::count_launch();
+      }
+      TK_CUDA(cudaGetLastError());
+      return TUCKER_OK;
+    }
+  }
+  // FP32 factors with a fiber level, two passes: fiber sums to HBM, then the pipelined
+  // update over fibers
   if (!bf16 && !(c->flags & (TUCKER_F_TF32X3 | TUCKER_F_UNPIPELINED)) && mc.fib && mc.fn_units > 0 && c->fib_T &&
       p.nother == 2 && pipe_shape(p.R[0], p.R[1])) {
     TtmcParams q = p;
