@@ -121,6 +121,15 @@ TUCKER_API tucker_status ttmc_mode(tucker_ctx *c, int mode, float *Y, void *stre
 TUCKER_API tucker_status qrp_leading(const double *A, int64_t m, int64_t n, int64_t lda, int k, double *Q,
                           int64_t *piv, double *rdiag, void *work, size_t work_bytes, void *stream);
 TUCKER_API size_t qrp_leading_work_bytes(int64_t m, int64_t n, int k);
+/*
+ * qrp_leading_sync_status — device-side outcome of the last qrp_leading that used `work`
+ * (its first bytes hold that call's error word, cleared by each call).  Synchronises
+ * `stream`, then returns TUCKER_ETIMEOUT if a bounded grid-wide wait gave up, TUCKER_ECUDA
+ * if a kernel found its launch shape or shared memory different from its plan, TUCKER_OK
+ * otherwise, and clears the word.  In both failure cases the call had written NaN into
+ * rdiag[0..k) and Q[0] and -1 into piv[0..k) and left the rest of Q unspecified.
+ */
+TUCKER_API tucker_status qrp_leading_sync_status(void *work, void *stream);
 
 /*
  * qrp_leading_noalloc — qrp_leading without caller-provided scratch, for callers that
@@ -134,12 +143,17 @@ TUCKER_API size_t qrp_leading_work_bytes(int64_t m, int64_t n, int k);
  * with qrp_leading_work_bytes(m, n, k) above that limit return TUCKER_EINVAL.  No
  * device memory is allocated by the call.  The first call on a device looks up the
  * array's device address (once per device, with that device current); make that
- * first call before any stream capture.  All calls share the array: whatever must
- * start at zero is cleared by each call, and calls that overlap on the GPU (different
- * streams, or different host threads on one device) race on it.
+ * first call before any stream capture.  The address is kept for the life of the
+ * process, so cudaDeviceReset on a device after its first call is not supported.  All
+ * calls share the array: whatever must start at zero is cleared by each call, and calls
+ * that overlap on the GPU (different streams, or different host threads on one device)
+ * race on it.
  */
 TUCKER_API tucker_status qrp_leading_noalloc(const double *A, int64_t m, int64_t n, int64_t lda, int k,
                                              double *Q, int64_t *piv, double *rdiag, void *stream);
+/* Device-side outcome of the last qrp_leading_noalloc on the current device, as
+ * qrp_leading_sync_status (the error word sits at the start of the fixed array). */
+TUCKER_API tucker_status qrp_leading_noalloc_sync_status(void *stream);
 TUCKER_API size_t qrp_leading_noalloc_max_bytes(void);
 
 /*
@@ -205,6 +219,25 @@ TUCKER_API void tucker_free(tucker_ctx *c);
  */
 TUCKER_API tucker_status tucker_set_profiling(tucker_ctx *c, int enable);
 TUCKER_API int tucker_phase_times(tucker_ctx *c, float *ms, int cap);
+/*
+ * Layout of one mode's sorted copy (instrumentation; no counterpart in the paper).  Writes
+ * up to `cap` int64 values to the host array `out`, in this order:
+ *   [0] non-empty slices S        [1] nonzeros per work unit (chunk)   [2] work units
+ *   [3] slices split over units   [4] 1 if the mode has a fiber level  [5] fibers F
+ *   [6] fibers per fiber unit     [7] fiber units                      [8] slices split over fiber units
+ *   [9] longest fiber (nonzeros)  [10] the middle remaining mode of the fiber level (0-based mode)
+ * Returns the number written, or -1 for a bad context, mode or pointer.
+ */
+TUCKER_API int tucker_mode_info(const tucker_ctx *c, int mode, int64_t *out, int cap);
+
+/*
+ * Measured FP32 FMA throughput of the current device in TFLOP/s (instrumentation; no
+ * counterpart in the paper): a grid of every SM's resident blocks runs `iters` x 128
+ * independent FMAs per thread, timed with CUDA events on `stream` (synchronises it);
+ * the best of three timed launches after one warm-up.  Returns -1 on a CUDA error.
+ */
+TUCKER_API double tucker_fp32_fma_tflops(int iters, void *stream);
+
 /* Number of kernels libtucker has launched in this process, over all contexts. */
 TUCKER_API uint64_t tucker_kernel_launches(void);
 

@@ -66,6 +66,17 @@ __global__ void gaussian_kernel(uint64_t seed, int mode, int64_t n, double *out)
   }
 }
 
+// Error word of a standalone QRP call: synchronise, read, clear, map to a status.
+tucker_status qrp_read_err_word(uint32_t *word, cudaStream_t s) {
+  uint32_t bits = 0;
+  if (cudaMemcpyAsync(&bits, word, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) return TUCKER_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return TUCKER_ECUDA;
+  if (!bits) return TUCKER_OK;
+  if (cudaMemsetAsync(word, 0, sizeof(uint32_t), s) != cudaSuccess) return TUCKER_ECUDA;
+  if (bits & kErrTimeout) return TUCKER_ETIMEOUT;
+  return TUCKER_ECUDA;
+}
+
 static tucker_status check_err_word(Ctx *c, cudaStream_t s) {
   uint32_t bits = 0;
   TK_CUDA(cudaMemcpyAsync(&bits, c->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
@@ -325,6 +336,16 @@ int tucker_phase_times(tucker_ctx *h, float *ms, int cap) {
 
 uint64_t tucker_kernel_launches(void) { return tk::g_launches.load(); }
 
+int tucker_mode_info(const tucker_ctx *h, int mode, int64_t *out, int cap) {
+  if (!h || !out || cap < 0 || mode < 0 || mode >= h->c.N) return -1;
+  const tk::ModeCopy &mc = h->c.mode[mode];
+  const int64_t v[] = {mc.S, mc.chunk, mc.n_units, mc.n_long, mc.fib ? 1 : 0, mc.F, mc.fchunk, mc.fn_units,
+                       mc.fn_long, (int64_t)tk::kFiberCap, mc.fib ? (int64_t)mc.other[mc.fmid_t] : -1};
+  const int n = std::min<int>(cap, (int)(sizeof(v) / sizeof(v[0])));
+  for (int i = 0; i < n; ++i) out[i] = v[i];
+  return n;
+}
+
 tucker_status tucker_selftest_wait(tucker_ctx *h, uint64_t max_polls, void *stream) {
   if (!h) return TUCKER_EINVAL;
   return tk::launch_wait_selftest(&h->c, (unsigned long long)max_polls, static_cast<cudaStream_t>(stream));
@@ -420,7 +441,12 @@ size_t qrp_leading_work_bytes(int64_t m, int64_t n, int k) {
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  return tk::qrp_work_bytes(m, n, k, sms);
+  return tk::kQrpErrWordBytes + tk::qrp_work_bytes(m, n, k, sms);
+}
+
+tucker_status qrp_leading_sync_status(void *work, void *stream) {
+  if (!work || reinterpret_cast<uintptr_t>(work) % 256) return TUCKER_EINVAL;
+  return tk::qrp_read_err_word(static_cast<uint32_t *>(work), static_cast<cudaStream_t>(stream));
 }
 
 tucker_status qrp_leading(const double *A, int64_t m, int64_t n, int64_t lda, int k, double *Q, int64_t *piv,
@@ -436,8 +462,12 @@ tucker_status qrp_leading(const double *A, int64_t m, int64_t n, int64_t lda, in
   int dev = 0, sms = 1;
   if (cudaGetDevice(&dev) != cudaSuccess) return TUCKER_ECUDA;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return TUCKER_ECUDA;
+  // the first bytes of the scratch hold the error word of this call (cleared here)
+  uint32_t *errw = static_cast<uint32_t *>(work);
+  if (cudaMemsetAsync(errw, 0, sizeof(uint32_t), static_cast<cudaStream_t>(stream)) != cudaSuccess) return TUCKER_ECUDA;
   tk::QrpWork w;
-  tk::qrp_bind_work(&w, work, m, n, k, sms);
+  tk::qrp_bind_work(&w, static_cast<char *>(work) + tk::kQrpErrWordBytes, m, n, k, sms);
+  w.err_out = errw;
   return tk::qrp_run_f64(A, m, n, lda, k, Q, k, piv, rdiag, &w, sms, static_cast<cudaStream_t>(stream));
 }
 

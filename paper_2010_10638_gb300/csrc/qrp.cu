@@ -24,6 +24,8 @@
 // last one; it waits for nobody, so there is no spin anywhere.
 #include <algorithm>
 #include <cfloat>
+#include <cstdlib>
+#include <cstring>
 
 #include "dfloat.cuh"
 #include "internal.cuh"
@@ -391,7 +393,7 @@ struct PArgs {
   int64_t ldq;
   int *flag, *nflag;
   unsigned *bar;   // [0] arrivals, [1] generation, [2] abort flag (cleared per call)
-  uint32_t *err;   // where a timeout is reported (the context's error word, or bar[2])
+  uint32_t *err;   // where a timeout is reported (the context's or the call's error word)
   int64_t *piv;
   double *rdiag;
   int64_t part_ld;
@@ -433,6 +435,8 @@ __device__ __forceinline__ void timeout_exit(const PArgs &a) {
     const double qnan = __longlong_as_double(0x7ff8000000000000ll);
     if (a.rdiag)
       for (int j = 0; j < a.k; ++j) a.rdiag[j] = qnan;
+    if (a.piv)
+      for (int j = 0; j < a.k; ++j) a.piv[j] = -1;
     a.Q[0] = qnan;  // a factor with a NaN makes the failure visible downstream
   }
 }
@@ -1109,7 +1113,10 @@ static tucker_status qrp_run(const AT *A, int64_t m, int64_t n, int64_t lda, int
                              int64_t *piv, double *rdiag, QrpWork *w, int nb, cudaStream_t s) {
   if (k == 0) return TUCKER_OK;
   if (k > 64) return TUCKER_ERANK;  // F rows are staged in 64-wide shared buffers
-  {
+  // TUCKER_QRP_FORM=multi runs the multi-kernel form below for every shape (a test and
+  // comparison switch); otherwise the single-launch forms are tried first
+  const char *form = std::getenv("TUCKER_QRP_FORM");
+  if (!(form && std::strcmp(form, "multi") == 0)) {
     cudaError_t e = cudaSuccess;
     if (qrp_cluster<AT>(A, m, n, lda, k, Q, ldq, piv, rdiag, w, s, &e))
       return e == cudaSuccess ? TUCKER_OK : TUCKER_ECUDA;

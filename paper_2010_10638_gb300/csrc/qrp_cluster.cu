@@ -744,6 +744,8 @@ __device__ void cbail(const CArgs &a) {
     const double qnan = __longlong_as_double(0x7ff8000000000000ll);
     if (a.rdiag)
       for (int j = 0; j < a.k; ++j) a.rdiag[j] = qnan;
+    if (a.piv)
+      for (int j = 0; j < a.k; ++j) a.piv[j] = -1;
     a.Q[0] = qnan;  // a factor with a NaN makes the failure visible downstream
   }
 }
@@ -759,8 +761,9 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
   tm.S = cl.num_blocks();
   tm.rank = cl.block_rank();
   tm.epoch = 0;
-  // The shared-memory carve-up below depends on the cluster shape: a launch whose shape
-  // differs from the plan (the same in every block) reports an error and touches nothing.
+  // The shared-memory carve-up below depends on the cluster shape and must fit the launch's
+  // dynamic shared memory: a launch whose shape or size differs from the plan (the same in
+  // every block) reports an error and touches nothing else.
   if ((int)tm.S != a.cluster || (int)gridDim.x != a.cluster * a.nclusters) {
     if (threadIdx.x == 0) atomicOr(a.err, kErrLaunch);
     return cbail(a);
@@ -768,6 +771,14 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
   const int64_t n = a.n, m = a.m;
   const int k = a.k, L = a.L;
   const CLayout lay = clayout(n, k, L, (int)tm.S, a.rows_per, a.rows_cached, (int)sizeof(AT));
+  {  // the carve-up must fit the dynamic shared memory this launch actually has
+    unsigned dyn;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+    if ((size_t)lay.total > (size_t)dyn) {
+      if (threadIdx.x == 0) atomicOr(a.err, kErrLaunch);
+      return cbail(a);
+    }
+  }
   tm.nown = (int)((n - (int64_t)tm.rank + tm.S - 1) / tm.S);
   const int64_t no = lay.no;
   double *Fo = reinterpret_cast<double *>(sm + lay.Fo);

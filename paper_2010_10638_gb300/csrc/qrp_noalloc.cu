@@ -9,7 +9,9 @@
 // loads this library holds it until the process exits.  In host code its name is
 // only a host-side stand-in, so the device address is looked up with
 // cudaGetSymbolAddress once per device, with that device current, on the first call
-// made on that device, and handed to the kernels as a plain pointer.
+// made on that device, and handed to the kernels as a plain pointer.  The address is
+// cached for the life of the process: a cudaDeviceReset after the first call on a
+// device unloads the module and makes the cached address stale, so it is not supported.
 #include <mutex>
 
 #include "internal.cuh"
@@ -59,11 +61,22 @@ tucker_status qrp_leading_noalloc(const double *A, int64_t m, int64_t n, int64_t
   tucker_status st = scratch_on_current_device(&scratch);
   if (st != TUCKER_OK) return st;
   // The QRP clears the parts of its workspace that must start at zero (its block
-  // counters and F) at the start of every call, so stale contents left by an earlier
-  // call are harmless; calls that overlap on the GPU share the array and race.
+  // counters, barrier words and F) at the start of every call, and this call clears its
+  // error word (the array's first bytes), so stale contents left by an earlier call are
+  // harmless; calls that overlap on the GPU share the array and race.
+  uint32_t *errw = static_cast<uint32_t *>(scratch);
+  if (cudaMemsetAsync(errw, 0, sizeof(uint32_t), static_cast<cudaStream_t>(stream)) != cudaSuccess) return TUCKER_ECUDA;
   tk::QrpWork w;
-  tk::qrp_bind_work(&w, scratch, m, n, k, sms);
+  tk::qrp_bind_work(&w, static_cast<char *>(scratch) + tk::kQrpErrWordBytes, m, n, k, sms);
+  w.err_out = errw;
   return tk::qrp_run_f64(A, m, n, lda, k, Q, k, piv, rdiag, &w, sms, static_cast<cudaStream_t>(stream));
+}
+
+tucker_status qrp_leading_noalloc_sync_status(void *stream) {
+  void *scratch = nullptr;
+  tucker_status st = scratch_on_current_device(&scratch);
+  if (st != TUCKER_OK) return st;
+  return tk::qrp_read_err_word(static_cast<uint32_t *>(scratch), static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

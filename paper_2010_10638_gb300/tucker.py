@@ -37,7 +37,8 @@ EXPORTS = ["tucker_init", "ttmc_mode", "qrp_leading", "qrp_leading_work_bytes", 
            "tucker_get_factor", "tucker_set_factor", "tucker_loss_grad", "tucker_nnz", "tucker_norm2",
            "tucker_sync_status", "tucker_free", "tucker_status_str", "tucker_last_error", "tucker_set_profiling",
            "tucker_phase_times", "tucker_kernel_launches", "qrp_leading_noalloc", "qrp_leading_noalloc_max_bytes",
-           "tucker_selftest_wait"]
+           "tucker_selftest_wait", "tucker_mode_info", "qrp_leading_sync_status",
+           "qrp_leading_noalloc_sync_status", "tucker_fp32_fma_tflops"]
 
 
 class TuckerError(RuntimeError):
@@ -92,6 +93,14 @@ def load(path: str = LIB_PATH):
     lib.qrp_leading_noalloc_max_bytes.restype = csz
     lib.tucker_selftest_wait.argtypes = [vp, u64, vp]
     lib.tucker_selftest_wait.restype = cint
+    lib.qrp_leading_sync_status.argtypes = [vp, vp]
+    lib.qrp_leading_sync_status.restype = cint
+    lib.qrp_leading_noalloc_sync_status.argtypes = [vp]
+    lib.qrp_leading_noalloc_sync_status.restype = cint
+    lib.tucker_fp32_fma_tflops.argtypes = [cint, vp]
+    lib.tucker_fp32_fma_tflops.restype = dbl
+    lib.tucker_mode_info.argtypes = [vp, cint, P(i64), cint]
+    lib.tucker_mode_info.restype = cint
     lib.tucker_kernel_launches.argtypes = []
     lib.tucker_kernel_launches.restype = ctypes.c_uint64
     for name in ("tucker_init", "ttmc_mode", "qrp_leading", "hooi_iter", "core_tensor", "tucker_get_factor",
@@ -305,6 +314,16 @@ def qrp_leading(A: torch.Tensor, k: int, work: torch.Tensor | None = None, strea
     return Q, piv, rdiag
 
 
+def qrp_leading_sync_status(work: torch.Tensor, stream=None) -> None:
+    """Raise if the last qrp_leading that used `work` gave up a bounded wait or found its
+    launch different from its plan (synchronises the stream)."""
+    _check(load().qrp_leading_sync_status(work.data_ptr(), _stream(stream)), "qrp_leading_sync_status")
+
+
+def qrp_leading_noalloc_sync_status(stream=None) -> None:
+    _check(load().qrp_leading_noalloc_sync_status(_stream(stream)), "qrp_leading_noalloc_sync_status")
+
+
 def tucker_set_profiling(ctx: Context, enable: bool = True) -> None:
     _check(load().tucker_set_profiling(ctx.handle, int(bool(enable))), "tucker_set_profiling", ctx)
 
@@ -317,6 +336,27 @@ def tucker_phase_times(ctx: Context):
     if got != n:
         raise TuckerError(6, "tucker_phase_times", "profiling off or no complete sweep")
     return [float(x) for x in buf]
+
+
+MODE_INFO_KEYS = ("slices", "chunk", "units", "long_slices", "fibers_on", "fibers", "fchunk", "fiber_units",
+                  "fiber_long_slices", "fiber_cap", "fiber_mid_mode")
+
+
+def tucker_mode_info(ctx: Context, mode: int) -> dict:
+    """Layout of one mode's sorted copy: slices, work units, fiber level (instrumentation)."""
+    buf = (ctypes.c_int64 * len(MODE_INFO_KEYS))()
+    got = load().tucker_mode_info(ctx.handle, int(mode), buf, len(MODE_INFO_KEYS))
+    if got != len(MODE_INFO_KEYS):
+        raise TuckerError(1, "tucker_mode_info")
+    return {k: int(v) for k, v in zip(MODE_INFO_KEYS, buf)}
+
+
+def tucker_fp32_fma_tflops(iters: int = 20000, stream=None) -> float:
+    """Measured FP32 FMA throughput of the current GPU (TFLOP/s)."""
+    v = float(load().tucker_fp32_fma_tflops(int(iters), _stream(stream)))
+    if v <= 0:
+        raise TuckerError(4, "tucker_fp32_fma_tflops")
+    return v
 
 
 def tucker_kernel_launches() -> int:
