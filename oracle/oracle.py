@@ -23,6 +23,10 @@ Functions and the passage each follows:
   loss_grad     - observed-entry loss 1/2 sum (x - [[G; U]])^2 and its gradients
   kron_count    - Kronecker rows formed so far (one per nonzero per mode, Section IV-C)
 
+``threads > 1`` (ttmc, qrp, gram, core, hooi) runs ``tucker_oracle_par.c``: the same loops
+split over POSIX threads by output column, equal to the serial results bit for bit (a CPU
+test checks this); it exists to time the oracle on all of a machine's cores.
+
 Parity status: every function above is pinned by tests under ``tests/`` against
 dense brute force, closed forms, LAPACK (scipy) or printed values of the paper.
 """
@@ -38,6 +42,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "tucker_oracle.c")
+_SRC_PAR = os.path.join(_HERE, "tucker_oracle_par.c")  # the same routines split over threads by column
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libtucker_oracle.so")
 _lib = None
@@ -46,9 +51,11 @@ _lib = None
 def build(force: bool = False) -> str:
     """Compile the C oracle (gcc -O2, no fast-math) into oracle/_build/."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_PAR))
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC, _SRC_PAR,
+                               "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -73,6 +80,15 @@ def _load():
         lib.orc_loss_grad.restype = None
         lib.orc_loss_grad.argtypes = [c_int, P(c_i64), P(c_int), c_i64, P(ctypes.c_uint32), P(c_dbl),
                                       P(P(c_dbl)), P(c_dbl), P(c_dbl), P(P(c_dbl)), P(c_dbl)]
+        lib.orc_ttmc_par.restype = None
+        lib.orc_ttmc_par.argtypes = [c_int, P(c_i64), P(c_int), c_i64, P(ctypes.c_uint32), P(c_dbl), c_int,
+                                     P(P(c_dbl)), P(c_dbl), c_int]
+        lib.orc_qrp_par.restype = c_int
+        lib.orc_qrp_par.argtypes = [P(c_dbl), c_i64, c_i64, c_i64, c_int, P(c_dbl), P(c_i64), P(c_dbl), c_int]
+        lib.orc_gram_par.restype = None
+        lib.orc_gram_par.argtypes = [P(c_dbl), c_i64, c_i64, P(c_dbl), c_int]
+        lib.orc_core_par.restype = None
+        lib.orc_core_par.argtypes = [c_i64, c_i64, c_int, P(c_dbl), P(c_dbl), P(c_dbl), c_int]
         lib.orc_kron_count.restype = c_i64
         lib.orc_kron_count.argtypes = []
         lib.orc_kron_reset.restype = None
@@ -122,9 +138,10 @@ def norm2(vals) -> float:
 
 
 # --------------------------------------------------------------------------- TTMc
-def ttmc(dims, ranks, coords, vals, mode, U):
+def ttmc(dims, ranks, coords, vals, mode, U, threads=1):
     """Y_(mode) = X_(mode) (kron_{m != mode} U_m), Alg. 2 inner loop, FP64.
-    Y is [I_mode, P] with the remaining modes ascending, last fastest (Alg. 4)."""
+    Y is [I_mode, P] with the remaining modes ascending, last fastest (Alg. 4).
+    threads > 1 splits the columns over host threads (same result bit for bit)."""
     lib = _load()
     N = len(dims)
     dims_a = np.asarray(dims, dtype=np.int64)
@@ -135,9 +152,12 @@ def ttmc(dims, ranks, coords, vals, mode, U):
     Us = [_f64(U[m]) if U[m] is not None else np.zeros((dims[m], ranks[m])) for m in range(N)]
     P = int(np.prod([ranks[m] for m in range(N) if m != mode], dtype=np.int64))
     Y = np.zeros((dims[mode], P), dtype=np.float64)
-    lib.orc_ttmc(N, _ptr(dims_a, ctypes.c_int64), _ptr(ranks_a, ctypes.c_int), nnz,
-                 _ptr(coords, ctypes.c_uint32), _ptr(vals, ctypes.c_double), mode, _ptr_array(Us),
-                 _ptr(Y, ctypes.c_double))
+    args = (N, _ptr(dims_a, ctypes.c_int64), _ptr(ranks_a, ctypes.c_int), nnz, _ptr(coords, ctypes.c_uint32),
+            _ptr(vals, ctypes.c_double), mode, _ptr_array(Us), _ptr(Y, ctypes.c_double))
+    if threads > 1:
+        lib.orc_ttmc_par(*args, int(threads))
+    else:
+        lib.orc_ttmc(*args)
     return Y
 
 
@@ -157,7 +177,7 @@ class QRPResult:
     rdiag: np.ndarray  # k diagonal entries of R
 
 
-def qrp(A, k):
+def qrp(A, k, threads=1):
     """Householder QR with column pivoting truncated at k reflectors (Section III-D)."""
     lib = _load()
     A = _f64(A)
@@ -165,33 +185,37 @@ def qrp(A, k):
     Q = np.zeros((m, k), dtype=np.float64)
     piv = np.zeros(k, dtype=np.int64)
     rdiag = np.zeros(k, dtype=np.float64)
-    rc = lib.orc_qrp(_ptr(A, ctypes.c_double), m, n, n, k, _ptr(Q, ctypes.c_double),
-                     _ptr(piv, ctypes.c_int64), _ptr(rdiag, ctypes.c_double))
+    args = (_ptr(A, ctypes.c_double), m, n, n, k, _ptr(Q, ctypes.c_double), _ptr(piv, ctypes.c_int64),
+            _ptr(rdiag, ctypes.c_double))
+    rc = lib.orc_qrp_par(*args, int(threads)) if threads > 1 else lib.orc_qrp(*args)
     if rc != 0:
         raise ValueError(f"qrp: k={k} exceeds min(m={m}, n={n})")
     return QRPResult(Q, piv, rdiag)
 
 
-def gram(Y):
+def gram(Y, threads=1):
     """Y Y^T (Section III-D, fat case)."""
     lib = _load()
     Y = _f64(Y)
     m, n = Y.shape
     S = np.zeros((m, m), dtype=np.float64)
-    lib.orc_gram(_ptr(Y, ctypes.c_double), m, n, _ptr(S, ctypes.c_double))
+    if threads > 1:
+        lib.orc_gram_par(_ptr(Y, ctypes.c_double), m, n, _ptr(S, ctypes.c_double), int(threads))
+    else:
+        lib.orc_gram(_ptr(Y, ctypes.c_double), m, n, _ptr(S, ctypes.c_double))
     return S
 
 
-def qrp_factor(Y, R, direct=False):
+def qrp_factor(Y, R, direct=False, threads=1):
     """The factor update of Alg. 2: U_n = QRP(Y_(n), R_n).  When Y_(n) is fat
     (P_n > I_n) the paper runs QRP on Y Y^T; ``direct`` keeps QRP on Y itself."""
     m, n = Y.shape
-    A = Y if (direct or n <= m) else gram(Y)
-    return qrp(A, R)
+    A = Y if (direct or n <= m) else gram(Y, threads)
+    return qrp(A, R, threads)
 
 
 # --------------------------------------------------------------------------- core
-def core(Y_last, U_last, ranks):
+def core(Y_last, U_last, ranks, threads=1):
     """G = Y x_N U_N^T  <=>  G_(N) = U_N^T Y_(N)  (Section III-B).  Returns G with shape ranks."""
     lib = _load()
     Y = _f64(Y_last)
@@ -199,7 +223,11 @@ def core(Y_last, U_last, ranks):
     I_N, P = Y.shape
     R_N = U.shape[1]
     G = np.zeros(P * R_N, dtype=np.float64)
-    lib.orc_core(I_N, P, R_N, _ptr(Y, ctypes.c_double), _ptr(U, ctypes.c_double), _ptr(G, ctypes.c_double))
+    args = (I_N, P, R_N, _ptr(Y, ctypes.c_double), _ptr(U, ctypes.c_double), _ptr(G, ctypes.c_double))
+    if threads > 1:
+        lib.orc_core_par(*args, int(threads))
+    else:
+        lib.orc_core(*args)
     return G.reshape(tuple(ranks))
 
 
@@ -219,11 +247,12 @@ class HOOIResult:
     rdiags: list
 
 
-def hooi(dims, ranks, coords, vals, U0, iters, direct=False, svd=False, coalesced=False):
+def hooi(dims, ranks, coords, vals, U0, iters, direct=False, svd=False, coalesced=False, threads=1):
     """Algorithm 2: sparse Tucker by HOOI with QRP (or SVD, Alg. 1, as a check).
 
     U0: list of initial factors (I_m x R_m); U0[0] is never read (mode 1 is the first
-    factor updated).  Returns the factors, the core and the fit after every sweep."""
+    factor updated).  Returns the factors, the core and the fit after every sweep.
+    threads > 1 runs the column-split routines (same results bit for bit)."""
     N = len(dims)
     if not coalesced:
         coords, vals = coalesce(coords, vals)
@@ -234,18 +263,18 @@ def hooi(dims, ranks, coords, vals, U0, iters, direct=False, svd=False, coalesce
     for _ in range(iters):
         pv, rd = [], []
         for n in range(N):
-            Y = ttmc(dims, ranks, coords, vals, n, U)
+            Y = ttmc(dims, ranks, coords, vals, n, U, threads)
             if svd:
                 Ul, _, _ = np.linalg.svd(Y, full_matrices=False)
                 U[n] = Ul[:, : ranks[n]].copy()
                 pv.append(None)
                 rd.append(None)
             else:
-                res = qrp_factor(Y, ranks[n], direct=direct)
+                res = qrp_factor(Y, ranks[n], direct=direct, threads=threads)
                 U[n] = res.Q
                 pv.append(res.piv)
                 rd.append(res.rdiag)
-        G = core(Y, U[N - 1], ranks)
+        G = core(Y, U[N - 1], ranks, threads)
         fits.append(fit_from_core(nx2, G))
         pivots.append(pv)
         rdiags.append(rd)
