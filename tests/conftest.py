@@ -19,10 +19,11 @@ def golden_dir():
     return GOLDEN
 
 
-@pytest.fixture(params=["cluster", "persistent"])
+@pytest.fixture(params=["cluster", "persistent", "multi"])
 def qrp_form(request, monkeypatch):
-    """Runs a test with each single-launch form of the QRP: the cluster form (one grid
-    barrier per reflector; the default wherever its shared-memory plan fits) and the
-    persistent cooperative form (two grid barriers per reflector)."""
+    """Runs a test with each form of the QRP: the cluster form (one grid barrier per
+    reflector; the default wherever its shared-memory plan fits), the persistent
+    cooperative form (two grid barriers per reflector), and the multi-kernel form (three
+    launches per reflector; what runs when neither single-launch form fits)."""
     monkeypatch.setenv("TUCKER_QRP_FORM", request.param)
     return request.param

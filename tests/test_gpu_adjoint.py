@@ -74,6 +74,70 @@ def test_completion_workload_sample_and_multilinear_identity():
         assert float(np.sum(dU[n].astype(np.float64) * U[n])) == pytest.approx(ref, rel=1e-4)
 
 
+def test_completion_10M_finite_differences_on_a_1000_entry_subsample():
+    """The completion workload's own check: 1,000 observed entries drawn (seeded) from the
+    completion-10M tensor itself, the parameters near the generating model.  The GPU
+    gradients (FP32) against central finite differences (h = 1e-6) of the FP64 oracle's
+    loss on the same entries, along four random directions over G and every U_m at once,
+    and on single entries of G and of factor rows the subsample touches; and against the
+    oracle's analytic gradients.  Bars: oracle vs finite differences 1e-6, GPU vs finite
+    differences and vs the oracle 1e-4 (relative to the derivative, or to the largest
+    entry of that gradient for single entries)."""
+    T = lib()
+    inst = synth.make("completion-10M")
+    w = inst.workload
+    rng = np.random.default_rng(55)
+    pick = np.sort(rng.choice(w.nnz, size=1000, replace=False))
+    coords = np.ascontiguousarray(inst.coords[:, pick])
+    vals = inst.vals[pick]
+    U = [(inst.model["U"][m] + 0.1 * rng.standard_normal(inst.model["U"][m].shape)).astype(np.float32)
+         for m in range(3)]
+    G = inst.model["G"].astype(np.float32)
+    _, L, dU, dG = gpu_loss_grad(w.dims, w.ranks, coords, vals, U, G)
+    U64 = [u.astype(np.float64) for u in U]
+    G64 = G.astype(np.float64)
+    v64 = vals.astype(np.float64)
+    Lr, dUr, dGr = oracle.loss_grad(w.dims, w.ranks, coords, v64, U64, G64)
+    assert L == pytest.approx(Lr, rel=TOL)
+    assert rel_fro(dG, dGr) <= TOL
+    for n in range(3):
+        assert rel_fro(dU[n], dUr[n]) <= TOL
+
+    def loss(Us, Gs):
+        return oracle.loss_grad(w.dims, w.ranks, coords, v64, Us, Gs)[0]
+
+    h = 1e-6
+    for _ in range(4):
+        D = [rng.standard_normal(u.shape) for u in U64]
+        DG = rng.standard_normal(G64.shape)
+        fd = (loss([u + h * d for u, d in zip(U64, D)], G64 + h * DG)
+              - loss([u - h * d for u, d in zip(U64, D)], G64 - h * DG)) / (2 * h)
+        an_o = sum(float(np.sum(d * g)) for d, g in zip(D, dUr)) + float(np.sum(DG * dGr))
+        an_g = sum(float(np.sum(d * g.astype(np.float64))) for d, g in zip(D, dU)) + float(np.sum(DG * dG))
+        assert abs(an_o - fd) <= 1e-6 * abs(fd)
+        assert abs(an_g - fd) <= TOL * abs(fd)
+    # single entries: 8 of the core, 8 of each factor in rows the subsample touches
+    for _ in range(8):
+        q = tuple(int(rng.integers(0, r)) for r in w.ranks)
+        Gp, Gm = G64.copy(), G64.copy()
+        Gp[q] += h
+        Gm[q] -= h
+        fd = (loss(U64, Gp) - loss(U64, Gm)) / (2 * h)
+        assert abs(float(dG[q]) - fd) <= TOL * float(np.max(np.abs(dGr)))
+        assert abs(float(dGr[q]) - fd) <= 1e-6 * float(np.max(np.abs(dGr)))
+    for m in range(3):
+        for _ in range(8):
+            i = int(coords[m, rng.integers(0, coords.shape[1])])
+            r = int(rng.integers(0, w.ranks[m]))
+            Up = [u.copy() for u in U64]
+            Um = [u.copy() for u in U64]
+            Up[m][i, r] += h
+            Um[m][i, r] -= h
+            fd = (loss(Up, G64) - loss(Um, G64)) / (2 * h)
+            assert abs(float(dU[m][i, r]) - fd) <= TOL * float(np.max(np.abs(dUr[m])))
+            assert abs(float(dUr[m][i, r]) - fd) <= 1e-6 * float(np.max(np.abs(dUr[m])))
+
+
 def test_directional_finite_difference_on_gpu():
     T = lib()
     rng = np.random.default_rng(9)

@@ -6,7 +6,8 @@ import pytest
 
 import oracle
 from paper_2010_10638_gb300 import synth
-from tests.gpu_util import lib, torch
+from tests.gpu_util import lib, rel_fro, torch
+from tests.hooi_canon import canonical
 
 pytestmark = pytest.mark.gpu
 
@@ -31,6 +32,12 @@ def check_against_oracle(w, iters, fit_tol=1e-6, **kw):
         np.testing.assert_allclose(U[n].T @ U[n], np.eye(ranks[n]), atol=1e-12)
         Pg, Po = U[n] @ U[n].T, ref.U[n] @ ref.U[n].T
         assert np.linalg.norm(Pg - Po) <= 1e-4 * np.sqrt(ranks[n])
+    # the core itself (Section III-B), with every factor column's sign fixed on both sides
+    Uc, Gc = canonical(U, G)
+    Uo, Go = canonical(ref.U, ref.G)
+    assert rel_fro(Gc, Go) <= 1e-4, f"core: relative error {rel_fro(Gc, Go):.2e}"
+    for n in range(len(dims)):
+        assert float(np.max(np.abs(Uc[n] - Uo[n]))) <= 1e-4
     return fits, ref
 
 

@@ -83,6 +83,8 @@ def test_qrp_rejects_bad_sizes():
 def test_qrp_runs_as_one_launch(qrp_form):
     """Factorisations with n <= 8192 run as one launch in either single-launch form (the
     multi-kernel form, kept for wider matrices, launches 3k + 3 kernels)."""
+    if qrp_form == "multi":
+        pytest.skip("the multi-kernel form launches 3k + 3 kernels by design")
     T = lib()
     rng = np.random.default_rng(5)
     for m, n, k in [(50_000, 256, 16), (1000, 256, 16), (40, 6, 4)]:
@@ -107,3 +109,25 @@ def test_qrp_cluster_form_on_a_tall_unfolding():
     np.testing.assert_array_equal(piv, ref.piv)
     np.testing.assert_allclose(rd, ref.rdiag, rtol=1e-11)
     np.testing.assert_allclose(Q, ref.Q, atol=1e-11)
+
+
+def test_multi_kernel_form_on_a_wide_matrix(monkeypatch):
+    """The multi-kernel form (3k + 3 launches) on a matrix wider than the persistent
+    form's 8192-column limit, forced, against the oracle; and its launch count."""
+    monkeypatch.setenv("TUCKER_QRP_FORM", "multi")
+    T = lib()
+    rng = np.random.default_rng(77)
+    m, n, k = 300, 10_000, 8
+    A = rng.standard_normal((m, n)) * rng.uniform(0.2, 5.0, n)
+    ref = oracle.qrp(A, k)
+    assert min_pivot_gap(A, k) > 1e-10
+    Ad = torch.as_tensor(A).cuda()
+    T.qrp_leading(Ad, k)
+    torch.cuda.synchronize()
+    before = T.tucker_kernel_launches()
+    Q, piv, rd = T.qrp_leading(Ad, k)
+    torch.cuda.synchronize()
+    assert T.tucker_kernel_launches() - before == 3 * k + 3
+    np.testing.assert_array_equal(piv.cpu().numpy(), ref.piv)
+    np.testing.assert_allclose(rd.cpu().numpy(), ref.rdiag, rtol=1e-11)
+    np.testing.assert_allclose(Q.cpu().numpy(), ref.Q, atol=1e-11)

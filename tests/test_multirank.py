@@ -66,7 +66,8 @@ def test_reference_arm_line_keeps_the_contract():
     the line's own value."""
     import json
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                        "--warmup", "0", "--oracle-nnz", "100000"], capture_output=True, text=True, timeout=300)
+                        "--warmup", "0", "--oracle-full", "0", "--oracle-nnz", "100000"], capture_output=True, text=True,
+                       timeout=300)
     assert r.returncode == 0, r.stderr
     d = json.loads(r.stdout.strip().splitlines()[-1])
     for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",

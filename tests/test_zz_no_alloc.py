@@ -40,6 +40,8 @@ def _call_with_work(L, A, k):
                        ctypes.c_void_p(work.data_ptr()), work.numel(),
                        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert rc == 0
+    assert L.qrp_leading_sync_status(ctypes.c_void_p(work.data_ptr()),
+                                     ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)) == 0
     torch.cuda.synchronize()
     return Q.cpu().numpy(), piv.cpu().numpy(), rd.cpu().numpy()
 
@@ -48,11 +50,13 @@ def test_noalloc_matches_qrp_leading_on_two_calls_in_a_row():
     T = lib()
     L = T.load()
     rng = np.random.default_rng(2024)
-    # a larger problem first, then a smaller one that runs on the scratch it left behind
-    for m, n, k in [(4000, 256, 16), (300, 40, 12)]:
+    # a larger problem first, then smaller ones that run on the scratch left behind; k = 48
+    # is beyond the cluster form (k <= 32) and runs the persistent form on the same array
+    for m, n, k in [(4000, 256, 16), (300, 40, 12), (3000, 128, 48)]:
         A = torch.as_tensor(rng.standard_normal((m, n)) * rng.uniform(0.2, 5.0, n)).cuda()
         assert L.qrp_leading_work_bytes(m, n, k) <= L.qrp_leading_noalloc_max_bytes()
         Q, piv, rd = _call_noalloc(L, A, k)
+        assert L.qrp_leading_noalloc_sync_status(ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)) == 0
         Qr, pivr, rdr = _call_with_work(L, A, k)
         np.testing.assert_array_equal(piv, pivr)
         np.testing.assert_allclose(rd, rdr, rtol=1e-11, atol=1e-12 * abs(rdr[0]))
