@@ -32,8 +32,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "sparse TTMc nonzeros/sec per mode and HOOI iteration time (s), % of HBM roofline"
 UNIT = "nonzeros/s per mode (N_modes * nnz / HOOI sweep time)"
-SM_COUNT, SM_MAX_MHZ, FP32_LANES = 152, 2070.0, 128
-FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12  # 80.5, from unit counts and max clock
 FP64_PEAK_TFLOPS_NOMINAL = 1.25
 L2_BYTES = 129 * 1024 * 1024
 
@@ -126,17 +124,44 @@ def profile_traffic(kernel_tag: str):
         return None
 
 
-def oracle_sample(inst, sample_nnz):
-    """The oracle on a bounded sample: one HOOI sweep over the first `sample_nnz` listed
-    entries of the same workload (same dims, ranks, initial factors).  Returns (seconds, nnz)."""
+def cpu_model():
+    """The host CPU's model name (x86 'model name', or the Arm implementer/part codes)."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            info = f.read()
+    except OSError:
+        return "unknown"
+    for key in ("model name", "Model", "Hardware"):
+        for line in info.splitlines():
+            if line.startswith(key) and ":" in line:
+                return line.split(":", 1)[1].strip()
+    parts = sorted({line.split(":", 1)[1].strip() for line in info.splitlines() if line.startswith("CPU part")})
+    impl = sorted({line.split(":", 1)[1].strip() for line in info.splitlines() if line.startswith("CPU implementer")})
+    return f"Arm implementer {','.join(impl)} part {','.join(parts)}" if parts else "unknown"
+
+
+def oracle_coalesced(inst, sample_nnz=None):
+    """The workload's listed entries (the first `sample_nnz`, or all), coalesced by the oracle."""
+    import oracle
+    n = inst.workload.nnz if sample_nnz is None else min(sample_nnz, inst.workload.nnz)
+    coords = np.ascontiguousarray(inst.coords[:, :n])
+    return oracle.coalesce(coords, inst.vals[:n].astype(np.float64))
+
+
+def oracle_sweep(inst, cc, cv, threads=1):
+    """Seconds of one oracle HOOI sweep (TTMc + QRP per mode, core, fit) on coalesced entries."""
     import oracle
     w = inst.workload
-    coords = np.ascontiguousarray(inst.coords[:, :sample_nnz])
-    vals = inst.vals[:sample_nnz].astype(np.float64)
-    cc, cv = oracle.coalesce(coords, vals)
     t0 = time.perf_counter()
-    oracle.hooi(w.dims, w.ranks, cc, cv, inst.U0, 1, coalesced=True)
-    return time.perf_counter() - t0, cc.shape[1]
+    oracle.hooi(w.dims, w.ranks, cc, cv, inst.U0, 1, coalesced=True, threads=threads)
+    return time.perf_counter() - t0
+
+
+def oracle_sample(inst, sample_nnz, threads=1):
+    """The oracle on a bounded sample: one HOOI sweep over the first `sample_nnz` listed
+    entries of the same workload (same dims, ranks, initial factors).  Returns (seconds, nnz)."""
+    cc, cv = oracle_coalesced(inst, sample_nnz)
+    return oracle_sweep(inst, cc, cv, threads), cc.shape[1]
 
 
 def max_over_ranks(value: float, device=None) -> float:
@@ -191,23 +216,24 @@ def run_reference(args):
     N = len(w.dims)
     steps = max(1, min(args.steps, 5))
     warm = min(args.warmup, 1)
-    sample = args.oracle_nnz
+    threads = os.cpu_count() or 1
+    cc, cv = oracle_coalesced(inst, None if args.oracle_full else args.oracle_nnz)
+    nz = cc.shape[1]
     for _ in range(warm):
-        oracle_sample(inst, sample)
-    times, nz = [], 0
-    for _ in range(steps):
-        t, nz = oracle_sample(inst, sample)
-        times.append(t)
+        oracle_sweep(inst, cc, cv, threads)
+    times = [oracle_sweep(inst, cc, cv, threads) for _ in range(steps)]
     tstep = sum(times) / len(times)
     value = N * nz / tstep
-    desc = (f"one oracle HOOI sweep (C, FP64, single thread) over the first {sample:,} listed entries of "
-            f"{w.name} ({nz:,} after coalescing), same dims/ranks/initial factors; {steps} timed of "
-            f"{args.steps} requested steps")
+    desc = (f"one oracle HOOI sweep (C, FP64, {threads} threads split by output column, results equal to the "
+            f"serial oracle bit for bit) over {'all' if args.oracle_full else f'the first {args.oracle_nnz:,} listed'} "
+            f"entries of {w.name} ({nz:,} after coalescing), same dims/ranks/initial factors; {steps} timed of "
+            f"{args.steps} requested steps; CPU: {cpu_model()}")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": steps,
             "warmup": warm, "ms_per_step": tstep * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "dims": list(w.dims), "nnz": w.nnz, "ranks": list(w.ranks)},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc,
+                             "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -398,6 +424,8 @@ def run_mine(args):
 
     # ---- roofline of the dominant kernel
     hbm_peak, hbm_src = peaks()
+    with torch.cuda.stream(stream):
+        fp32_peak = T.tucker_fp32_fma_tflops(20000, stream=stream)
     ttmc_total = sum(phase_ms[2 * n] for n in range(N))
     qrp_total = sum(phase_ms[2 * n + 1] for n in range(N))
     flops = [2.0 * ctx.P(n) * Zc for n in range(N)]
@@ -405,12 +433,19 @@ def run_mine(args):
     ttmc_avg_ms = sum(ttmc_ms) / N
     ttmc_flops = sum(flops) / N
     ttmc_bytes = sum(bytes_alg) / N
-    ttmc_roof = {"kernel": "FP32 TTMc: ttmc_pipe_kernel<16,16,4,4> (+ fixup); modes whose fibers are at most 1/4 of "
-                           "the nonzeros run ttmc_fibsum_kernel<16> then the same kernel over fibers", "bound": "alu",
-                 "achieved": ttmc_flops / (ttmc_avg_ms * 1e-3) / 1e12, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                 "frac": ttmc_flops / (ttmc_avg_ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
+    forms = []
+    for n in range(N):
+        mi = T.tucker_mode_info(ctx, n)
+        forms.append("fiber form (ttmc_fibsum_kernel + ttmc_pipe_kernel over fibers, "
+                     f"{mi['fibers'] / max(Zc, 1):.2f} fibers per nonzero)" if mi["fibers_on"]
+                     else "nonzero form (ttmc_pipe_kernel)")
+    ttmc_roof = {"kernel": "FP32 TTMc per mode: " + "; ".join(f"mode {n + 1} {f}" for n, f in enumerate(forms)),
+                 "bound": "alu",
+                 "achieved": ttmc_flops / (ttmc_avg_ms * 1e-3) / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                 "frac": ttmc_flops / (ttmc_avg_ms * 1e-3) / 1e12 / fp32_peak,
                  "traffic": profile_traffic("ttmc_fp32_skew-20M"),
-                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                 "peak_source": "measured in this run: FP32 FMA throughput kernel (tucker_fp32_fma_tflops)",
+                 "binding_unit": "L1/shared-memory path (operand and row loads) and instruction issue; see profiles/",
                  "hbm_view": {"achieved_gbs": ttmc_bytes / (ttmc_avg_ms * 1e-3) / 1e9, "peak_gbs": hbm_peak,
                               "frac": ttmc_bytes / (ttmc_avg_ms * 1e-3) / 1e9 / hbm_peak,
                               "peak_source": hbm_src, "alg_bytes_per_launch": ttmc_bytes},
@@ -424,21 +459,42 @@ def run_mine(args):
         qbytes.append((k_ + 1) * m_ * n_ * 4.0 + 2.0 * m_ * k_ * 8.0)
     q_ms = sum(phase_ms[2 * n + 1] for n in big) / len(big)
     q_bytes = sum(qbytes) / len(qbytes)
+    one_pass = sum(w.dims[n] * ctx.P(n) * 4.0 + 2.0 * w.dims[n] * w.ranks[n] * 8.0 for n in big) / len(big)
+    k_q = w.ranks[big[0]]
     qrp_roof = {"kernel": f"qrp_cluster_kernel<float> on the {max(w.dims)} x {ctx.P(big[0])} unfoldings",
-                "bound": "hbm", "achieved": q_bytes / (q_ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
-                "frac": q_bytes / (q_ms * 1e-3) / 1e9 / hbm_peak,
-                "traffic": profile_traffic("qrp_cluster_50000x256"),
-                "peak_source": hbm_src, "alg_bytes_per_launch": q_bytes, "avg_launch_ms": q_ms,
-                "note": "k+1 passes over Y, part of it held in shared memory and the rest read from L2 (DRAM "
-                        "traffic is about one pass); bound by the per-reflector synchronisation and FP64 latency"}
+                "bound": "latency",
+                "achieved": one_pass / (q_ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                "frac": one_pass / (q_ms * 1e-3) / 1e9 / hbm_peak,
+                "traffic": None,
+                "peak_source": hbm_src, "dram_bytes_per_launch": one_pass, "avg_launch_ms": q_ms,
+                "us_per_reflector": q_ms * 1e3 / k_q,
+                "note": "DRAM traffic is about one pass over the FP32 Y plus V and Q (the other k passes of the "
+                        "column sums read shared memory and L2); the step is bound by the k dependent reflector "
+                        "steps (one grid barrier, a cluster reduction and FP64 dependent chains each), not by a "
+                        "memory or arithmetic roof; traffic is not captured (the kernel is kept off ncu)"}
     dominant = ttmc_roof if ttmc_total >= qrp_total else qrp_roof
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        t, nz = oracle_sample(inst, args.oracle_nnz)
-        cpu = {"value": N * nz / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"one oracle HOOI sweep (C, FP64, single thread) over the first {args.oracle_nnz:,} listed "
-                         f"entries of {w.name} ({nz:,} after coalescing); {t:.1f} s"}
+        threads = os.cpu_count() or 1
+        cc, cv = oracle_coalesced(inst, None if args.oracle_full else args.oracle_nnz)
+        t_all = oracle_sweep(inst, cc, cv, threads)
+        t1, nz1 = oracle_sample(inst, args.oracle_single_nnz, threads=1)
+        cpu = {"value": N * cc.shape[1] / t_all, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"one oracle HOOI sweep (C, FP64, {threads} threads split by output column, equal to the "
+                         f"serial oracle bit for bit) over {cc.shape[1]:,} coalesced entries of {w.name}; "
+                         f"{t_all:.1f} s",
+               "cpu_model": cpu_model(),
+               "single_thread": {"value": N * nz1 / t1, "cores": 1,
+                                 "sample": f"one serial oracle sweep over the first {args.oracle_single_nnz:,} listed "
+                                           f"entries ({nz1:,} after coalescing); {t1:.1f} s"}}
+
+    paper = {}
+    if rank == 0 and not args.no_paper:
+        import oracle
+        oracle.build()
+        paper["fig7_sparsity_sweep"] = fig7_rows(T, torch, os.cpu_count() or 1)
+        paper["table3_core_ttm"] = table3_rows(T, torch, os.cpu_count() or 1)
 
     clocks = clk.summary()
     value = world * N * Zc / (ms_per_step * 1e-3)
@@ -447,7 +503,10 @@ def run_mine(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name, "dims": list(w.dims), "nnz": w.nnz, "nnz_coalesced": Zc,
                        "ranks": list(w.ranks), "l2": "flushed between timed steps (256 MiB write)",
-                       "precision": "TTMc FP32, QRP/core/fit FP64", "replicas": world},
+                       "precision": "TTMc FP32 (FP32 products and sums); QRP: FP64 storage, norms, reflectors, R "
+                                    "and T, with A^T y summed in double-float FP32 pairs around a power-of-two "
+                                    "offset (about 2^-49 s1 per product) and Q formed as double-float sums; core "
+                                    "and fit FP64", "replicas": world},
             "hooi_s_per_iter": ms_per_step * 1e-3,
             "phases_ms": {"ttmc": [phase_ms[2 * n] for n in range(N)], "qrp": [phase_ms[2 * n + 1] for n in range(N)],
                           "core_fit": phase_ms[2 * N]},
@@ -455,7 +514,7 @@ def run_mine(args):
             "roofline": dominant, "roofline_other": qrp_roof if dominant is ttmc_roof else ttmc_roof,
             "init_s": init_s, "fit_after_warmup_and_steps": fit,
             "bf16_factor_form": bf16, "tf32x3_form": tf32x3, "adjoint_form": adjoint, "e2e": e2e, "cpu_baseline": cpu,
-            "clocks": clocks, "gpu_launches": int(launches)}
+            "clocks": clocks, "gpu_launches": int(launches), **paper}
     if rank == 0:
         print(json.dumps(line), flush=True)
     T.tucker_free(ctx)
@@ -491,46 +550,40 @@ def _gpu_sweeps(T, torch, inst, iters, profile=False):
     return init_s, ms, fits, ctx, phases
 
 
-def run_fig7(args):
+def fig7_rows(T, torch, threads=1):
     """Section IV-C, Fig. 7: whole decompositions of 200^3 random tensors, ranks 16, over a
     range of sparsities; GPU (init + sweeps) beside the FP64 oracle on the host."""
-    import torch
     import oracle
-    from paper_2010_10638_gb300 import build as libbuild, synth, tucker as T
-    libbuild.build()
-    T.load()
-    oracle.build()
+    from paper_2010_10638_gb300 import synth
     rows = []
     for i in range(len(synth.FIG7_DENSITIES)):
         inst = synth.make(synth.fig7_workload(i))
         w = inst.workload
-        _gpu_sweeps(T, torch, inst, 2)  # warm-up (first-use set-up of the kernels)
+        _, _, _, ctx, _ = _gpu_sweeps(T, torch, inst, 2)  # warm-up (first-use set-up of the kernels)
+        T.tucker_free(ctx)
         init_s, ms, fits, ctx, _ = _gpu_sweeps(T, torch, inst, w.iters)
         T.tucker_free(ctx)
         t0 = time.perf_counter()
-        ref = oracle.hooi(w.dims, w.ranks, inst.coords, inst.vals.astype(np.float64), inst.U0, w.iters)
+        ref = oracle.hooi(w.dims, w.ranks, inst.coords, inst.vals.astype(np.float64), inst.U0, w.iters,
+                          threads=threads)
         t_or = time.perf_counter() - t0
         gpu_s = init_s + sum(ms) * 1e-3
         rows.append({"sparsity": w.nnz / float(np.prod(w.dims)), "nnz": w.nnz, "sweeps": w.iters,
                      "gpu_s": gpu_s, "gpu_init_s": init_s, "gpu_sweep_ms": float(np.median(ms)),
-                     "oracle_s": t_or, "oracle_cores": 1, "speedup_vs_oracle": t_or / gpu_s,
+                     "oracle_s": t_or, "oracle_cores": threads, "speedup_vs_oracle": t_or / gpu_s,
+                     "max_fit_diff_vs_oracle": float(np.max(np.abs(np.asarray(fits) - np.asarray(ref.fits)))),
                      "fit_gpu": fits[-1], "fit_oracle": float(ref.fits[-1])})
-    print(json.dumps({"experiment": "fig7 sparsity sweep", "dims": [200, 200, 200], "ranks": [16, 16, 16],
-                      "data": "synthetic, distinct uniform coordinates, U(0,1) values", "rows": rows}), flush=True)
-    return 0
+    return {"experiment": "fig7 sparsity sweep (Section IV-C)", "dims": [200, 200, 200], "ranks": [16, 16, 16],
+            "data": "synthetic, distinct uniform coordinates, U(0,1) values", "rows": rows}
 
 
-def run_table3(args):
+def table3_rows(T, torch, threads=1):
     """Table III: the dense core TTM, a 32 x 32 x I3 tensor times a 32 x I3 factor, as the
     core step of one sweep on a fully listed 32 x 32 x I3 tensor (ranks 32); the core
     phase is timed with CUDA events inside hooi_iter, beside the oracle's core on the
-    same Y_(3) and U_3."""
-    import torch
+    same Y_(3) and U_3 (and its difference from the GPU's core)."""
     import oracle
-    from paper_2010_10638_gb300 import build as libbuild, synth, tucker as T
-    libbuild.build()
-    T.load()
-    oracle.build()
+    from paper_2010_10638_gb300 import synth
     rows = []
     for i in range(len(synth.TABLE3_I3)):
         inst = synth.make(synth.table3_workload(i))
@@ -539,18 +592,41 @@ def run_table3(args):
         core_ms = float(np.median([p[-1] for p in phases[2:]]))
         Y3 = T.ttmc_mode(ctx, 2).cpu().numpy().astype(np.float64)
         U3 = T.tucker_get_factor(ctx, 2).cpu().numpy()
+        Gg = T.core_tensor(ctx).cpu().numpy()
         T.tucker_free(ctx)
         reps = 20
         t0 = time.perf_counter()
         for _ in range(reps):
-            oracle.core(Y3, U3, w.ranks)
+            Go = oracle.core(Y3, U3, w.ranks, threads)
         t_or = (time.perf_counter() - t0) / reps
         flops = 2.0 * 32 * 32 * w.dims[2] * 32
         rows.append({"I3": w.dims[2], "core_fit_ms": core_ms, "gflops": flops / (core_ms * 1e-3) / 1e9,
-                     "oracle_ms": t_or * 1e3, "oracle_cores": 1})
-    print(json.dumps({"experiment": "table3 core TTM", "shape": "(32 x 32 x I3) x_3 (32 x I3)^T -> 32 x 32 x 32",
-                      "note": "core_fit_ms is the core step of hooi_iter (core tensor, its norm and the fit)",
-                      "rows": rows}), flush=True)
+                     "oracle_ms": t_or * 1e3, "oracle_cores": threads,
+                     "core_rel_diff_vs_oracle": float(np.linalg.norm(Gg - Go) / np.linalg.norm(Go))})
+    return {"experiment": "table3 core TTM (Section IV-A)", "shape": "(32 x 32 x I3) x_3 (32 x I3)^T -> 32 x 32 x 32",
+            "note": "core_fit_ms is the core step of hooi_iter (core tensor, its norm and the fit); the oracle's "
+                    "core is computed from the GPU's Y_(3) and U_3", "rows": rows}
+
+
+def run_fig7(args):
+    import torch
+    import oracle
+    from paper_2010_10638_gb300 import build as libbuild, tucker as T
+    libbuild.build()
+    T.load()
+    oracle.build()
+    print(json.dumps(fig7_rows(T, torch, os.cpu_count() or 1)), flush=True)
+    return 0
+
+
+def run_table3(args):
+    import torch
+    import oracle
+    from paper_2010_10638_gb300 import build as libbuild, tucker as T
+    libbuild.build()
+    T.load()
+    oracle.build()
+    print(json.dumps(table3_rows(T, torch, os.cpu_count() or 1)), flush=True)
     return 0
 
 
@@ -573,6 +649,7 @@ def run_configs(args):
     except (OSError, ValueError):
         pass
     rows = []
+    fp32_peak = T.tucker_fp32_fma_tflops(20000)
     for name in ("tiny-100^3", "zipf-10k^3", "order4-5M", "skew-20M"):
         inst = synth.make(name)
         w = inst.workload
@@ -604,7 +681,7 @@ def run_configs(args):
             if bf16:
                 row["ttmc_tensor_frac"] = tflops / bf16_peak
             else:
-                row["ttmc_fp32_frac"] = tflops / FP32_PEAK_TFLOPS
+                row["ttmc_fp32_frac"] = tflops / fp32_peak
             if not bf16:
                 t_s, nz = oracle_sample(inst, min(args.oracle_nnz, w.nnz))
                 row["oracle_s_per_iter"] = t_s * Zc / nz
@@ -626,11 +703,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--workload", default="skew-20M")
-    ap.add_argument("--oracle-nnz", type=int, default=1_000_000)
+    ap.add_argument("--oracle-nnz", type=int, default=1_000_000,
+                    help="entries the threaded oracle sweeps when --oracle-full is off")
+    ap.add_argument("--oracle-full", type=int, default=1, help="1: the threaded oracle sweeps the whole workload")
+    ap.add_argument("--oracle-single-nnz", type=int, default=1_000_000,
+                    help="entries of the single-thread oracle sample")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-bf16", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-paper", action="store_true", help="leave the Fig. 7 and Table III curves out of the line")
     ap.add_argument("--fig7", action="store_true", help="Fig. 7 sparsity sweep (200^3, ranks 16) instead")
     ap.add_argument("--table3", action="store_true", help="Table III core TTM shapes instead")
     ap.add_argument("--configs", action="store_true", help="every workload recipe at full size instead")
