@@ -211,6 +211,7 @@ static tucker_status init_impl(Ctx *c, const uint32_t *coords, const float *vals
     dev_free(c, g);
   }
   for (int m = 0; m < N; ++m) refresh_factor_copies(c, m, s);
+  if (c->flags & TUCKER_F_BF16_FACTORS) make_factor_maps(c);
   TK_CUDA(cudaGetLastError());
   TK_CUDA(cudaStreamSynchronize(s));
   c->astream = 0;  // the caller may destroy s; later allocations name their own stream

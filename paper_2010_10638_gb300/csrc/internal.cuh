@@ -2,6 +2,7 @@
 // Not part of the public ABI (see include/tucker.h).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -105,6 +106,10 @@ struct Ctx {
   double *U64[kMaxOrder] = {};        // FP64 master factors
   float *U32[kMaxOrder] = {};         // FP32 copies read by the TTMc
   __nv_bfloat16 *U16[kMaxOrder] = {}; // BF16 copies (TUCKER_F_BF16_FACTORS)
+  // TMA descriptors of the BF16 copies (rows of one factor, one row per box) for the row
+  // gathers of the pipelined BF16 TTMc; tm16_ok[m] false where none could be made
+  CUtensorMap tm16[kMaxOrder] = {};
+  bool tm16_ok[kMaxOrder] = {};
 
   float *Y = nullptr;          // TTMc output of the current mode (max I_n * P_n floats)
   float *carry = nullptr;      // partial rows of split slices (max n_units * P_n floats)
@@ -161,6 +166,8 @@ tucker_status build_sorted_copies(Ctx *c, const uint32_t *coords, const float *v
 
 // ---- K-b: TTMc (ttmc.cu)
 tucker_status launch_ttmc(Ctx *c, int mode, float *Y, cudaStream_t s);
+// TMA descriptors of the BF16 factor copies (host only; no device work)
+void make_factor_maps(Ctx *c);
 // 0, 1, ..., n-1 and n ones (the index and value streams of the fiber form's update pass)
 void fill_iota_ones(uint32_t *iota, float *ones, int64_t n, cudaStream_t s);
 // TTMc of mode `mode` with values `val` (in that mode's sorted order) and FP32 factors

@@ -45,6 +45,7 @@ struct TtmcParams {
   float *Y;
   float *carry;
   int64_t P;
+  uint32_t *err;         // the context's error word (bounded waits that gave up)
   const uint32_t *fptr;  // fiber form: [F+1] first nonzero of each fiber (positions above are fibers)
   const uint32_t *fmid;  // fiber form: [F] index of the first remaining mode of each fiber
 };
@@ -1144,6 +1145,230 @@ __global__ void __launch_bounds__(kTtmcWarps * 32) ttmc_bf16_kernel(const TtmcPa
   }
 }
 
+// ============================================================================ TMA-fed BF16 form
+// The arithmetic of ttmc_bf16_kernel (order 3, ranks 16 x 16) with the factor rows brought
+// into shared memory by the tensor memory accelerator instead of by the warp's own loads:
+// each warp keeps a ring of kTmaStages tiles (32 nonzeros each); for every tile, sixteen
+// lanes issue one cp.async.bulk.tensor gather4 each (four rows of U_a or U_b of 32 bytes),
+// completing on the stage's mbarrier.  The rows of tile t + kTmaStages are requested as
+// soon as tile t has been consumed, so a warp has up to kTmaStages tiles of gathers in
+// flight and holds none of them in registers.  The value x_z is applied to the A
+// fragments after ldmatrix, in FP32 and rounded to BF16 as the staging of ttmc_bf16_kernel
+// does, so both kernels give the same Y bit for bit.  Every wait is bounded; a warp whose
+// wait gives up records kErrTimeout, waits (bounded) for its copies in flight and leaves.
+constexpr int kTmaWarps = 4;
+constexpr int kTmaStages = 4;
+constexpr int kTmaRows = 48;                       // 32 rows per tile + 16 zero rows read past the tile
+constexpr unsigned long long kTmaSpin = 1ull << 22;  // polls of an mbarrier before a wait gives up
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, unsigned parity) {
+  uint32_t done;
+  asm volatile(
+      "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// bounded wait for the phase with the given parity; false when it gave up
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, unsigned parity) {
+  for (unsigned long long i = 0; i < kTmaSpin; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (i > 64) __nanosleep(32);
+  }
+  return false;
+}
+// four rows r0..r3 of a row-major factor (one box = one row) to dst (4 x row bytes)
+__device__ __forceinline__ void tma_gather4(uint32_t dst, const CUtensorMap *tm, uint32_t r0, uint32_t r1,
+                                            uint32_t r2, uint32_t r3, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cta.global.tile::gather4.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+      "%4, %5, %6}], [%7];" ::"r"(dst),
+      "l"(tm), "r"(0), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(bar)
+      : "memory");
+}
+
+template <int PL, int RB>
+__global__ void __launch_bounds__(kTmaWarps * 32) ttmc_bf16_tma_kernel(const TtmcParams p,
+                                                                       const __grid_constant__ CUtensorMap tmA,
+                                                                       const __grid_constant__ CUtensorMap tmB) {
+  static_assert(PL == 16 && RB == 16, "one gather4 box per 32-byte row");
+  constexpr int MT = PL / 16, NT = RB / 8;
+  constexpr int STAGE = kTmaRows * (PL + RB);  // BF16 elements per stage
+  constexpr unsigned TX = 32u * (PL + RB) * 2u;  // bytes a stage receives
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __nv_bfloat16 *ring = reinterpret_cast<__nv_bfloat16 *>(smem_raw) + (size_t)w * kTmaStages * STAGE;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + (size_t)kTmaWarps * kTmaStages * STAGE * 2) + w * kTmaStages;
+  const int64_t u = (int64_t)blockIdx.x * kTmaWarps + w;
+  if (u >= p.n_units) return;
+  const uint32_t e0 = __ldg(p.unit_e0 + u);
+  const uint32_t e_end = (u + 1 < p.n_units) ? __ldg(p.unit_e0 + u + 1) : p.Z;
+  const int slot = __ldg(p.unit_slot + u);
+  const int ntiles = (int)((e_end - e0 + 31u) / 32u);
+  const int g = lane >> 2, t4 = lane & 3;
+  auto As = [&](int st) { return ring + st * STAGE; };
+  auto Bs = [&](int st) { return ring + st * STAGE + kTmaRows * PL; };
+  auto bar = [&](int st) { return (uint32_t)__cvta_generic_to_shared(bars + st); };
+  // zero tails (never written by the copies), barriers
+  for (int st = 0; st < kTmaStages; ++st) {
+    for (int q = lane; q < 16 * PL; q += 32) As(st)[32 * PL + q] = __float2bfloat16(0.f);
+    for (int q = lane; q < 16 * RB; q += 32) Bs(st)[32 * RB + q] = __float2bfloat16(0.f);
+  }
+  if (lane == 0)
+    for (int st = 0; st < kTmaStages; ++st) mbar_init(bar(st), 1u);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncwarp();
+
+  // requests the rows of tile tt into stage st (indices of its positions, lane = position)
+  auto issue = [&](int tt, uint32_t ia, uint32_t ib) {
+    const int st = tt % kTmaStages;
+    if (lane == 0) mbar_expect_tx(bar(st), TX);
+    __syncwarp();
+    const int q = lane & 7;  // lanes q and 8 + q request rows 4q .. 4q + 3 of U_a and U_b
+    const uint32_t a0 = __shfl_sync(kFull, ia, 4 * q), a1 = __shfl_sync(kFull, ia, 4 * q + 1);
+    const uint32_t a2 = __shfl_sync(kFull, ia, 4 * q + 2), a3 = __shfl_sync(kFull, ia, 4 * q + 3);
+    const uint32_t b0 = __shfl_sync(kFull, ib, 4 * q), b1 = __shfl_sync(kFull, ib, 4 * q + 1);
+    const uint32_t b2 = __shfl_sync(kFull, ib, 4 * q + 2), b3 = __shfl_sync(kFull, ib, 4 * q + 3);
+    if (lane < 8) {
+      tma_gather4((uint32_t)__cvta_generic_to_shared(As(st) + 4 * q * PL), &tmA, a0, a1, a2, a3, bar(st));
+    } else if (lane < 16) {
+      tma_gather4((uint32_t)__cvta_generic_to_shared(Bs(st) + 4 * q * RB), &tmB, b0, b1, b2, b3, bar(st));
+    }
+  };
+  // indices of tile tt (positions past the unit read row 0, a valid row, and are masked)
+  auto tile_idx = [&](int tt, uint32_t &ia, uint32_t &ib) {
+    const uint32_t pos = e0 + 32u * (uint32_t)tt + (uint32_t)lane;
+    ia = (pos < e_end) ? __ldg(p.idx[0] + pos) : 0u;
+    ib = (pos < e_end) ? __ldg(p.idx[1] + pos) : 0u;
+  };
+  const int pro = ntiles < kTmaStages ? ntiles : kTmaStages;
+  for (int tt = 0; tt < pro; ++tt) {
+    uint32_t ia, ib;
+    tile_idx(tt, ia, ib);
+    issue(tt, ia, ib);
+  }
+
+  float acc[MT][NT][4];
+#pragma unroll
+  for (int i = 0; i < MT; ++i)
+#pragma unroll
+    for (int jn = 0; jn < NT; ++jn)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[i][jn][q] = 0.f;
+  uint32_t kb = __ldg(p.unit_k0 + u);
+  uint32_t bound = (kb + 1u + lane <= p.S) ? __ldg(p.sptr + kb + 1u + lane) : 0xffffffffu;
+  float x = (e0 + lane < e_end) ? __ldg(p.val + e0 + lane) : 0.f;
+  int failed_at = -1;
+  for (int t = 0; t < ntiles; ++t) {
+    const int st = t % kTmaStages;
+    const uint32_t e = e0 + 32u * (uint32_t)t;
+    const int nt = (int)min(32u, e_end - e);
+    const uint32_t q = bound - e;
+    uint32_t starts = __reduce_or_sync(kFull, q < 32u ? (1u << q) : 0u);
+    starts &= (nt >= 32) ? kFull : ((1u << nt) - 1u);
+    const uint32_t kp = kb + __popc(starts & ((2u << lane) - 1u));
+    const bool end_is_start = __any_sync(kFull, q == (uint32_t)nt);
+    const uint32_t kb_next = kb + __popc(__ballot_sync(kFull, q <= (uint32_t)nt));
+    // loads of the next tile's slice offsets and values, and of the indices of the tile
+    // whose rows are requested after this one is consumed
+    const uint32_t bound_next = (kb_next + 1u + lane <= p.S) ? __ldg(p.sptr + kb_next + 1u + lane) : 0xffffffffu;
+    const uint32_t posn = e + 32u + (uint32_t)lane;
+    const float xn = (posn < e_end) ? __ldg(p.val + posn) : 0.f;
+    uint32_t ia_f = 0u, ib_f = 0u;
+    if (t + kTmaStages < ntiles) tile_idx(t + kTmaStages, ia_f, ib_f);
+    if (!__all_sync(kFull, mbar_wait(bar(st), (unsigned)((t / kTmaStages) & 1)))) {
+      failed_at = t;
+      break;
+    }
+    const __nv_bfloat16 *A = As(st), *B = Bs(st);
+    uint32_t segs = starts | 1u;
+    while (segs) {
+      const int p0 = __ffs(segs) - 1;
+      segs &= segs - 1u;
+      const int p1 = segs ? (__ffs(segs) - 1) : nt;
+      for (int ks = p0; ks < p1; ks += 16) {
+        const int k0 = ks + 2 * t4, k8 = k0 + 8;
+        const float x0 = __shfl_sync(kFull, x, k0 & 31), x1 = __shfl_sync(kFull, x, (k0 + 1) & 31);
+        const float x8 = __shfl_sync(kFull, x, k8 & 31), x9 = __shfl_sync(kFull, x, (k8 + 1) & 31);
+        const uint32_t m0 = (k0 < p1 ? 0x0000ffffu : 0u) | (k0 + 1 < p1 ? 0xffff0000u : 0u);
+        const uint32_t m8 = (k8 < p1 ? 0x0000ffffu : 0u) | (k8 + 1 < p1 ? 0xffff0000u : 0u);
+        const int mrow = lane & 7, msel = lane >> 3;
+        uint32_t bfr[NT][2];
+#pragma unroll
+        for (int nq = 0; nq < NT; nq += 2) {
+          const int kr = ks + mrow + ((msel & 1) ? 8 : 0);
+          const int nc = nq * 8 + ((msel & 2) ? 8 : 0);
+          uint32_t r[4];
+          ldsm_x4_trans(r, B + kr * RB + nc);
+          bfr[nq][0] = r[0];
+          bfr[nq][1] = r[1];
+          bfr[nq + 1][0] = r[2];
+          bfr[nq + 1][1] = r[3];
+        }
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) {
+          const int kr = ks + mrow + ((msel & 2) ? 8 : 0);
+          const int mc = mt * 16 + ((msel & 1) ? 8 : 0);
+          uint32_t a[4];
+          ldsm_x4_trans(a, A + kr * PL + mc);
+          // x_z on the A fragments: a0, a1 hold nonzeros k0, k0 + 1; a2, a3 hold k8, k8 + 1
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&a[r]));
+            const float lo = (r < 2) ? x0 : x8, hi = (r < 2) ? x1 : x9;
+            const __nv_bfloat162 h = __floats2bfloat162_rn(f.x * lo, f.y * hi);
+            a[r] = *reinterpret_cast<const uint32_t *>(&h);
+          }
+          a[0] &= m0;
+          a[1] &= m0;
+          a[2] &= m8;
+          a[3] &= m8;
+#pragma unroll
+          for (int nq = 0; nq < NT; ++nq) mma_bf16(acc[mt][nq], a, bfr[nq][0], bfr[nq][1]);
+        }
+      }
+      const bool flush = (p1 < nt) || end_is_start || (e + (uint32_t)nt == e_end);
+      if (flush) {
+        const uint32_t kseg = __shfl_sync(kFull, kp, p0);
+        float *dst = (slot >= 0) ? p.carry + (size_t)slot * p.P : p.Y + (size_t)__ldg(p.sid + kseg) * p.P;
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+          for (int nq = 0; nq < NT; ++nq) {
+            const int row = mt * 16 + g, col = nq * 8 + 2 * t4;
+            *reinterpret_cast<float2 *>(dst + (size_t)row * RB + col) = make_float2(acc[mt][nq][0], acc[mt][nq][1]);
+            *reinterpret_cast<float2 *>(dst + (size_t)(row + 8) * RB + col) =
+                make_float2(acc[mt][nq][2], acc[mt][nq][3]);
+            acc[mt][nq][0] = acc[mt][nq][1] = acc[mt][nq][2] = acc[mt][nq][3] = 0.f;
+          }
+      }
+    }
+    __syncwarp();  // every lane has read stage st
+    if (t + kTmaStages < ntiles) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(t + kTmaStages, ia_f, ib_f);
+    }
+    kb = kb_next;
+    bound = bound_next;
+    x = xn;
+  }
+  if (failed_at >= 0) {  // record, then let the copies still in flight land before the warp leaves
+    if (lane == 0) atomicOr(p.err, kErrTimeout);
+    // tiles failed_at .. failed_at + S - 1 (below ntiles) were requested and not consumed:
+    // one outstanding phase per stage
+    for (int tt = failed_at; tt < failed_at + kTmaStages && tt < ntiles; ++tt)
+      mbar_wait(bar(tt % kTmaStages), (unsigned)((tt / kTmaStages) & 1));
+  }
+}
+
 template <int NL, int PL, int RB, int MODE, typename FT>
 __global__ void __launch_bounds__(kTtmcWarps * 32) ttmc_mma_kernel(const TtmcParams p) {
   static_assert(PL % 16 == 0 && RB % 8 == 0, "mma tiles");
@@ -1456,6 +1681,28 @@ static cudaError_t run_bf16(const TtmcParams &p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <int PL, int RB>
+static cudaError_t run_bf16_tma(const TtmcParams &p, const CUtensorMap &tmA, const CUtensorMap &tmB, cudaStream_t s) {
+  const size_t smem = (size_t)kTmaWarps * kTmaStages * (kTmaRows * (PL + RB) * 2 + sizeof(uint64_t));
+  auto kern = ttmc_bf16_tma_kernel<PL, RB>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const unsigned blocks = (unsigned)((p.n_units + kTmaWarps - 1) / kTmaWarps);
+  kern<<<blocks, kTmaWarps * 32, smem, s>>>(p, tmA, tmB);
+  ::tk::count_launch();
+  return cudaGetLastError();
+}
+
+// TUCKER_TTMC_TMA=1 runs the BF16 form on ttmc_bf16_tma_kernel (rows gathered by the TMA).
+// Same Y bit for bit, but slower on the 20M-nonzero skewed workload (0.59 / 0.92 / 0.90 ms
+// against 0.34 / 0.24 / 0.29 ms per mode): a tile of 32 nonzeros needs 16 gather4 requests
+// of 128 bytes, and the copy engine completes one such request per ~28 SM cycles, well
+// below the rate at which the warps' own 16-byte loads bring the same rows.  Kept opt-in.
+static bool tma_rows() {
+  const char *e = std::getenv("TUCKER_TTMC_TMA");
+  return e && e[0] == '1';
+}
+
 template <int NL, int PL, int RB, int MODE, typename FT>
 static cudaError_t run_mma(const TtmcParams &p, cudaStream_t s) {
   if constexpr (MODE == kBf16) return run_bf16<NL, PL, RB>(p, s);
@@ -1639,6 +1886,7 @@ static tucker_status ttmc_impl(Ctx *c, int mode, float *Y, const float *val, con
   p.Y = Y;
   p.carry = c->carry;
   p.P = mc.P;
+  p.err = c->d_err;
   // A fiber level, opt-in fused kernel (fiber sums kept on chip), FP32 or BF16 factors
   if (!(c->flags & (TUCKER_F_TF32X3 | TUCKER_F_UNPIPELINED)) && mc.fib && mc.n_units > 0 && mc.unit_f0 &&
       p.nother == 2 && fused_fibers()) {
@@ -1720,9 +1968,15 @@ static tucker_status ttmc_impl(Ctx *c, int mode, float *Y, const float *val, con
   if (mc.n_units > 0) {
     cudaError_t err = cudaSuccess;
     bool done = false;
-    if (bf16)  // the BF16-factor form runs on the tensor cores
-      done = dispatch_mma<kBf16, __nv_bfloat16>(p, s, &err);
-    else if (c->flags & TUCKER_F_TF32X3)  // opt-in FP32-class form on the tensor cores
+    if (bf16) {  // the BF16-factor form runs on the tensor cores
+      if (p.nother == 2 && p.R[0] == 16 && p.R[1] == 16 && c->tm16_ok[mc.other[0]] && c->tm16_ok[mc.other[1]] &&
+          tma_rows()) {  // rows gathered by the TMA into a ring of tiles
+        err = run_bf16_tma<16, 16>(p, c->tm16[mc.other[0]], c->tm16[mc.other[1]], s);
+        done = true;
+      } else {
+        done = dispatch_mma<kBf16, __nv_bfloat16>(p, s, &err);
+      }
+    } else if (c->flags & TUCKER_F_TF32X3)  // opt-in FP32-class form on the tensor cores
       done = dispatch_mma<kTf32x3, float>(p, s, &err);
     else if (!(c->flags & TUCKER_F_UNPIPELINED))
       done = dispatch_pipe(p, s, &err);
@@ -1741,6 +1995,36 @@ static tucker_status ttmc_impl(Ctx *c, int mode, float *Y, const float *val, con
     TK_CUDA(cudaGetLastError());
   }
   return TUCKER_OK;
+}
+
+// TMA descriptors of the BF16 factor copies: a 2-D tensor I_m x R_m (rows of R_m * 2 bytes),
+// one row per box, so that a gather4 copy fetches four rows.  Built with the driver's
+// cuTensorMapEncodeTiled, looked up through the runtime (no link against the driver).
+void make_factor_maps(Ctx *c) {
+  using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  void *fn = nullptr;
+  cudaDriverEntryPointQueryResult q{};
+  for (int m = 0; m < c->N; ++m) c->tm16_ok[m] = false;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn) {
+    cudaGetLastError();
+    return;
+  }
+  auto encode = reinterpret_cast<EncodeFn>(fn);
+  for (int m = 0; m < c->N; ++m) {
+    const int R = c->ranks[m];
+    if (!c->U16[m] || (R * 2) % 16 != 0 || c->dims[m] > 0xffffffffLL) continue;
+    const cuuint64_t dims[2] = {(cuuint64_t)R, (cuuint64_t)c->dims[m]};
+    const cuuint64_t strides[1] = {(cuuint64_t)R * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)R, 1};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = encode(&c->tm16[m], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, c->U16[m], dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    c->tm16_ok[m] = (r == CUDA_SUCCESS);
+  }
 }
 
 tucker_status launch_ttmc(Ctx *c, int mode, float *Y, cudaStream_t s) {

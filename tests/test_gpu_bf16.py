@@ -58,3 +58,24 @@ def test_tf32x3_form_matches_fp32_form(name, dims, ranks, nnz):
     for n in range(len(dims)):
         ya, yb = T.ttmc_mode(a, n), T.ttmc_mode(b, n)
         assert rel_fro(ya.cpu().numpy(), yb.cpu().numpy()) <= 2e-6
+
+
+@pytest.mark.parametrize("name,nnz", [("zipf-10k^3", 200_000), ("skew-20M", 300_000)])
+def test_tma_fed_bf16_form_equals_register_staged_form(name, nnz, monkeypatch):
+    """The opt-in BF16 form whose factor rows arrive by TMA row gathers (gather4 into a
+    4-stage shared-memory ring, mbarrier completion) computes the same products in the
+    same order as the register-staged BF16 form: Y equal bit for bit on every mode."""
+    T = lib()
+    w = synth.make(name, nnz=nnz)
+    ctx = T.tucker_init(w.workload.dims, torch.as_tensor(w.coords.astype(np.int32)).cuda(),
+                        torch.as_tensor(w.vals).cuda(), w.workload.ranks, [torch.as_tensor(u).cuda() for u in w.U0],
+                        bf16=True)
+    for n in range(3):
+        monkeypatch.setenv("TUCKER_TTMC_TMA", "0")
+        Y0 = T.ttmc_mode(ctx, n).clone()
+        monkeypatch.setenv("TUCKER_TTMC_TMA", "1")
+        Y1 = T.ttmc_mode(ctx, n).clone()
+        torch.cuda.synchronize()
+        T.tucker_sync_status(ctx)  # no bounded wait gave up
+        assert torch.equal(Y0, Y1), f"mode {n}"
+    T.tucker_free(ctx)

@@ -1,6 +1,8 @@
 """GPU HOOI (Algorithm 2: TTMc -> QRP per mode, then the core and the fit) against the
 FP64 oracle: the fit after every sweep within 1e-6, the factors' subspaces and the
 core tensor close, pivot choices identical."""
+import os
+
 import numpy as np
 import pytest
 
@@ -26,7 +28,7 @@ def check_against_oracle(w, iters, fit_tol=1e-6, **kw):
     dims, ranks = w.workload.dims, w.workload.ranks
     ctx, fits, U, G = gpu_hooi(dims, ranks, w.coords, w.vals, w.U0, iters, **kw)
     ref = oracle.hooi(dims, ranks, w.coords, w.vals.astype(np.float64), w.U0, iters,
-                      direct=kw.get("direct", False))
+                      direct=kw.get("direct", False), threads=os.cpu_count() or 1)
     np.testing.assert_allclose(fits, ref.fits, rtol=0, atol=fit_tol)
     for n in range(len(dims)):
         np.testing.assert_allclose(U[n].T @ U[n], np.eye(ranks[n]), atol=1e-12)

@@ -71,7 +71,8 @@ def test_zipf_1M_ten_sweeps_live_against_oracle():
     inst = synth.make("zipf-10k^3")
     w = inst.workload
     fits, U, G, _, _ = gpu_run(inst)
-    ref = oracle.hooi(w.dims, w.ranks, inst.coords, inst.vals.astype(np.float64), inst.U0, w.iters)
+    ref = oracle.hooi(w.dims, w.ranks, inst.coords, inst.vals.astype(np.float64), inst.U0, w.iters,
+                      threads=os.cpu_count() or 1)
     np.testing.assert_allclose(fits, ref.fits, rtol=0, atol=FIT_TOL)
     Uo, Go = canonical(ref.U, ref.G)
     check_model(U, G, Go, [sketch(Uo[n], n) for n in range(3)], w.ranks, ref.rdiags[-1])

@@ -14,6 +14,8 @@ bases of R^32 whose column order only a pivot decision fixes); its Frobenius nor
 no choice of basis changes, always within 1e-6 relative (FP32 TTMc).  I3 = 64 and 256:
 at I3 = 32 every factor keeps its whole space, G holds all of X, and the fit is the square
 root of a difference at the rounding level of the FP32 Y (no fixed bar on it there)."""
+import os
+
 import numpy as np
 import pytest
 
@@ -45,7 +47,7 @@ def test_fig7_sparsity_point_matches_oracle(index):
     w = inst.workload
     assert all(r * r > d for r, d in zip(w.ranks, w.dims))  # P_n = 256 > I_n = 200: the Gram branch
     fits, U, G = gpu_hooi(inst, w.iters)
-    rec, Uo, Go = oracle_sweeps(inst)
+    rec, Uo, Go = oracle_sweeps(inst, threads=os.cpu_count() or 1)
     assert min(min(g) for g in rec["min_gap"]) > 1e-8
     np.testing.assert_allclose(fits, rec["fits"], rtol=0, atol=1e-6)
     Uc, Gc = canonical(U, G)
@@ -62,7 +64,7 @@ def test_table3_core_ttm_shape_matches_oracle(index):
     assert inst.coords.shape[1] == int(np.prod(w.dims))  # every entry listed
     iters = 2
     fits, U, G = gpu_hooi(inst, iters)
-    rec, Uo, Go = oracle_sweeps(inst, iters=iters)
+    rec, Uo, Go = oracle_sweeps(inst, iters=iters, threads=os.cpu_count() or 1)
     np.testing.assert_allclose(fits, rec["fits"], rtol=0, atol=1e-6)
     assert np.linalg.norm(G) == pytest.approx(np.linalg.norm(Go), rel=1e-6)
     for n, u in enumerate(U):
