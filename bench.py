@@ -274,8 +274,10 @@ def run_mine(args):
         fit_buf = torch.zeros(1, dtype=torch.float64, device=dev)
         flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
 
+        # the timed step: one sweep replayed from a CUDA graph of the whole iteration (the
+        # first call runs one sweep eagerly and captures the next)
         for _ in range(args.warmup):
-            T.hooi_iter(ctx, fit_buf, stream=stream)
+            T.tucker_hooi_graph(ctx, 1, fit_buf, stream=stream)
         torch.cuda.synchronize()
 
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -288,7 +290,7 @@ def run_mine(args):
             for i in range(args.steps):
                 flush.fill_(float(i))  # evict L2 between timed steps (outside the events)
                 starts[i].record(stream)
-                T.hooi_iter(ctx, fit_buf, stream=stream)
+                T.tucker_hooi_graph(ctx, 1, fit_buf, stream=stream)
                 ends[i].record(stream)
             torch.cuda.synchronize()
         launches = T.tucker_kernel_launches() - launches0
@@ -301,6 +303,18 @@ def run_mine(args):
 
         # max over ranks
         ms_per_step = max_over_ranks(ms_per_step, dev)
+
+        # the same sweep launched kernel by kernel (hooi_iter), for comparison
+        eager = []
+        for i in range(20):
+            flush.fill_(float(i))
+            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_.record(stream)
+            T.hooi_iter(ctx, fit_buf, stream=stream)
+            b_.record(stream)
+            eager.append((a_, b_))
+        torch.cuda.synchronize()
+        eager_ms = statistics.median(a_.elapsed_time(b_) for a_, b_ in eager)
 
         # per-phase split of a sweep (profiling pass, events inside the library)
         T.tucker_set_profiling(ctx, True)
@@ -508,6 +522,8 @@ def run_mine(args):
                                     "offset (about 2^-49 s1 per product) and Q formed as double-float sums; core "
                                     "and fit FP64", "replicas": world},
             "hooi_s_per_iter": ms_per_step * 1e-3,
+            "step": "one HOOI sweep (TTMc + QRP per mode, core, fit) replayed from a CUDA graph of the whole iteration",
+            "eager_ms_per_step": eager_ms,
             "phases_ms": {"ttmc": [phase_ms[2 * n] for n in range(N)], "qrp": [phase_ms[2 * n + 1] for n in range(N)],
                           "core_fit": phase_ms[2 * N]},
             "ttmc_nnz_per_s_per_mode": [Zc / (t * 1e-3) for t in ttmc_ms],

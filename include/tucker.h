@@ -167,6 +167,23 @@ TUCKER_API size_t qrp_leading_noalloc_max_bytes(void);
 TUCKER_API tucker_status hooi_iter(tucker_ctx *c, double *fit_out, void *stream);
 
 /*
+ * tucker_hooi_graph — `sweeps` sweeps of hooi_iter (Algorithm 2) replayed from a CUDA graph
+ * of one sweep: the whole iteration (every mode's TTMc, QRP and factor refresh, the core
+ * and the fit) is one graph launch, without per-kernel launch overhead or host work
+ * between its kernels.  The results are those of hooi_iter, bit for bit.
+ *   fit_out  device double: the fit of each sweep is written there (the last one remains);
+ *            fixed at the first call (the graph writes to it)
+ *   stream   a stream other than the legacy default stream (graph capture needs one)
+ * The first call on a context runs one sweep as hooi_iter does (which also completes
+ * every one-time set-up of the kernels), then captures the next sweep into a graph and
+ * replays it for the remaining sweeps; later calls replay the graph.  TUCKER_EINVAL for a
+ * NULL stream or fit pointer, or a fit pointer other than the first call's; errors of the
+ * capture are TUCKER_ECUDA.  A later tucker_set_factor keeps the graph valid (it reads
+ * the factors in place).
+ */
+TUCKER_API tucker_status tucker_hooi_graph(tucker_ctx *c, int sweeps, double *fit_out, void *stream);
+
+/*
  * core_tensor — the core of the last sweep, G_(N) = U_N^T Y_(N) (Section III-B,
  * eqs. ttm_ele and core_unfolded).  G: device double [R_1 * ... * R_N], C-order.
  * TUCKER_ESTATE before the first hooi_iter or after tucker_set_factor.

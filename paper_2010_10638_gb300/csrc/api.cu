@@ -33,6 +33,8 @@ static const char *const kQrpRange[kMaxOrder] = {"qrp mode 0", "qrp mode 1", "qr
 
 static std::atomic<uint64_t> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+uint64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+void count_launches(int64_t delta) { g_launches.fetch_add((uint64_t)delta, std::memory_order_relaxed); }
 
 __global__ void f64_to_f32_kernel(const double *in, int64_t n, float *out32, __nv_bfloat16 *out16) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -284,6 +286,66 @@ static tucker_status hooi_impl(Ctx *c, double *fit_out, cudaStream_t s) {
   return TUCKER_OK;
 }
 
+// One sweep captured into a CUDA graph, replayed `sweeps` times.  hooi_impl with a device
+// fit pointer makes no host synchronisation and allocates nothing, so it captures as is.
+static tucker_status hooi_graph_impl(Ctx *c, int sweeps, double *fit_out, cudaStream_t s) {
+  if (c->sweep_graph && fit_out != c->graph_fit) {
+    c->last_error = "tucker_hooi_graph: the fit pointer differs from the one the graph was captured with";
+    return TUCKER_EINVAL;
+  }
+  const uint32_t saved_flags = c->flags;
+  const bool saved_prof = c->profiling;
+  c->flags |= TUCKER_F_FIT_DEVICE;  // the fit goes to fit_out on the device inside the graph
+  c->profiling = false;             // no event records inside the graph
+  tucker_status st = TUCKER_OK;
+  int done = 0;
+  if (!c->sweep_graph) {
+    if (sweeps > 0) {  // one eager sweep: it also completes every one-time set-up of the kernels
+      st = hooi_impl(c, fit_out, s);
+      ++done;
+    }
+    cudaGraph_t g = nullptr;
+    if (st == TUCKER_OK) {
+      cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        const uint64_t before = launches_so_far();
+        const tucker_status cs = hooi_impl(c, fit_out, s);
+        e = cudaStreamEndCapture(s, &g);
+        // the captured launches did not run: count them on every replay instead
+        c->graph_kernels = launches_so_far() - before;
+        count_launches(-(int64_t)c->graph_kernels);
+        if (cs != TUCKER_OK) st = cs;
+      }
+      if (st == TUCKER_OK && e == cudaSuccess) e = cudaGraphInstantiate(&c->sweep_graph, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (st == TUCKER_OK && e != cudaSuccess) {
+        c->last_error = std::string("tucker_hooi_graph: capture of a sweep failed: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        c->sweep_graph = nullptr;
+        st = TUCKER_ECUDA;
+      }
+      if (st == TUCKER_OK) {
+        c->graph_fit = fit_out;
+        --c->sweeps;  // the captured sweep did not run
+      }
+    }
+  }
+  for (; st == TUCKER_OK && done < sweeps; ++done) {
+    const cudaError_t e = cudaGraphLaunch(c->sweep_graph, s);
+    if (e != cudaSuccess) {
+      c->last_error = std::string("cudaGraphLaunch: ") + cudaGetErrorString(e);
+      st = TUCKER_ECUDA;
+      break;
+    }
+    count_launches((int64_t)c->graph_kernels);
+    ++c->sweeps;
+  }
+  if (st == TUCKER_OK && done > 0) c->G_valid = true;
+  c->flags = saved_flags;
+  c->profiling = saved_prof;
+  return st;
+}
+
 }  // namespace tk
 
 // ============================================================================ C ABI
@@ -314,6 +376,7 @@ void tucker_free(tucker_ctx *c) {
   cudaStreamSynchronize(0);
   for (cudaEvent_t e : c->c.ev)
     if (e) cudaEventDestroy(e);
+  if (c->c.sweep_graph) cudaGraphExecDestroy(c->c.sweep_graph);
   delete c;
 }
 
@@ -399,6 +462,12 @@ tucker_status ttmc_mode(tucker_ctx *h, int mode, float *Y, void *stream) {
 tucker_status hooi_iter(tucker_ctx *h, double *fit_out, void *stream) {
   if (!h) return TUCKER_EINVAL;
   return tk::hooi_impl(&h->c, fit_out, static_cast<cudaStream_t>(stream));
+}
+
+tucker_status tucker_hooi_graph(tucker_ctx *h, int sweeps, double *fit_out, void *stream) {
+  if (!h || !fit_out || !stream || sweeps < 0) return TUCKER_EINVAL;
+  tk::Range r("tucker_hooi_graph");
+  return tk::hooi_graph_impl(&h->c, sweeps, fit_out, static_cast<cudaStream_t>(stream));
 }
 
 tucker_status core_tensor(tucker_ctx *h, double *G, void *stream) {

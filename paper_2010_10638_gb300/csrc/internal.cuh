@@ -140,6 +140,11 @@ struct Ctx {
   cudaEvent_t ev[2 * kMaxOrder + 2] = {};
   int n_ev = 0;
 
+  // one HOOI sweep captured as a CUDA graph (tucker_hooi_graph), with the fit destination
+  cudaGraphExec_t sweep_graph = nullptr;
+  double *graph_fit = nullptr;
+  uint64_t graph_kernels = 0;  // library kernels in one replay of the graph
+
   std::vector<void *> allocs;  // every device allocation, freed by tucker_free
   cudaStream_t astream = 0;    // the stream allocations and frees are ordered on (the current call's)
   std::string last_error;
@@ -147,6 +152,8 @@ struct Ctx {
 
 // ---- instrumentation: kernels launched by this library (process-wide)
 void count_launch();
+uint64_t launches_so_far();
+void count_launches(int64_t delta);  // graph replays add their kernels; captures remove theirs
 
 // ---- allocation (host-side failure injection for tests: TUCKER_FAIL_ALLOC_AT=k fails the k-th)
 cudaError_t dev_alloc(Ctx *c, void **p, size_t bytes);

@@ -38,7 +38,7 @@ EXPORTS = ["tucker_init", "ttmc_mode", "qrp_leading", "qrp_leading_work_bytes", 
            "tucker_sync_status", "tucker_free", "tucker_status_str", "tucker_last_error", "tucker_set_profiling",
            "tucker_phase_times", "tucker_kernel_launches", "qrp_leading_noalloc", "qrp_leading_noalloc_max_bytes",
            "tucker_selftest_wait", "tucker_mode_info", "qrp_leading_sync_status",
-           "qrp_leading_noalloc_sync_status", "tucker_fp32_fma_tflops"]
+           "qrp_leading_noalloc_sync_status", "tucker_fp32_fma_tflops", "tucker_hooi_graph"]
 
 
 class TuckerError(RuntimeError):
@@ -97,6 +97,8 @@ def load(path: str = LIB_PATH):
     lib.qrp_leading_sync_status.restype = cint
     lib.qrp_leading_noalloc_sync_status.argtypes = [vp]
     lib.qrp_leading_noalloc_sync_status.restype = cint
+    lib.tucker_hooi_graph.argtypes = [vp, cint, vp, vp]
+    lib.tucker_hooi_graph.restype = cint
     lib.tucker_fp32_fma_tflops.argtypes = [cint, vp]
     lib.tucker_fp32_fma_tflops.restype = dbl
     lib.tucker_mode_info.argtypes = [vp, cint, P(i64), cint]
@@ -349,6 +351,19 @@ def tucker_mode_info(ctx: Context, mode: int) -> dict:
     if got != len(MODE_INFO_KEYS):
         raise TuckerError(1, "tucker_mode_info")
     return {k: int(v) for k, v in zip(MODE_INFO_KEYS, buf)}
+
+
+def tucker_hooi_graph(ctx: Context, sweeps: int, fit: torch.Tensor, stream=None) -> None:
+    """`sweeps` HOOI sweeps replayed from a CUDA graph of one sweep; the fit of each sweep
+    goes to the device float64 tensor `fit` (the same tensor on every call).  `stream` must
+    not be the legacy default stream (a torch.cuda.Stream, say)."""
+    _dev(fit, torch.float64, "fit")
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if _stream(stream) == 0:
+        raise ValueError("tucker_hooi_graph: a stream other than the legacy default stream is needed")
+    _check(load().tucker_hooi_graph(ctx.handle, int(sweeps), fit.data_ptr(), _stream(stream)), "tucker_hooi_graph",
+           ctx)
 
 
 def tucker_fp32_fma_tflops(iters: int = 20000, stream=None) -> float:
