@@ -330,7 +330,7 @@ def run_mine(args):
         ttmc_ms = time_ttmc_modes(T, torch, ctx, w.dims, dev, stream, flush)
 
         # BF16-factor form on the same workload
-        bf16 = tf32x3 = None
+        bf16 = None
         if not args.no_bf16:
             ctxb = T.tucker_init(w.dims, coords_d, vals_d, w.ranks, U0_d, bf16=True, fit_device=True, stream=stream)
             bms = time_ttmc_modes(T, torch, ctxb, w.dims, dev, stream, flush)
@@ -350,11 +350,6 @@ def run_mine(args):
                                           zip([4.0 * N * Zc + 4.0 * w.dims[n] * ctx.P(n) + 4.0 * (w.dims[n] + 1)
                                                for n in range(N)], bms)]}
             T.tucker_free(ctxb)
-            # opt-in FP32-class form on tensor cores (3xTF32)
-            ctxt = T.tucker_init(w.dims, coords_d, vals_d, w.ranks, U0_d, tf32x3=True, fit_device=True, stream=stream)
-            tms = time_ttmc_modes(T, torch, ctxt, w.dims, dev, stream, flush)
-            tf32x3 = {"ttmc_ms_per_mode": tms, "ttmc_nnz_per_s_per_mode": [Zc / (t * 1e-3) for t in tms]}
-            T.tucker_free(ctxt)
 
     # ---- the differentiation form: loss + adjoint on the completion workload
     adjoint = None
@@ -529,7 +524,7 @@ def run_mine(args):
             "ttmc_nnz_per_s_per_mode": [Zc / (t * 1e-3) for t in ttmc_ms],
             "roofline": dominant, "roofline_other": qrp_roof if dominant is ttmc_roof else ttmc_roof,
             "init_s": init_s, "fit_after_warmup_and_steps": fit,
-            "bf16_factor_form": bf16, "tf32x3_form": tf32x3, "adjoint_form": adjoint, "e2e": e2e, "cpu_baseline": cpu,
+            "bf16_factor_form": bf16, "adjoint_form": adjoint, "e2e": e2e, "cpu_baseline": cpu,
             "clocks": clocks, "gpu_launches": int(launches), **paper}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -56,8 +56,6 @@ typedef enum {
 #define TUCKER_F_QRP_DIRECT 0x2u   /* fat Y_(n) (P_n > I_n): QRP on Y_(n) itself, not on Y Y^T */
 #define TUCKER_F_HOST_INPUT 0x4u   /* coords, vals and U0 given to tucker_init are host pointers */
 #define TUCKER_F_FIT_DEVICE 0x8u   /* hooi_iter writes the fit through a device pointer, no sync */
-#define TUCKER_F_TF32X3 0x10u      /* FP32 form of the TTMc on tensor cores (3xTF32 split: about
-                                      1e-6 relative error instead of FP32 rounding); default off */
 #define TUCKER_F_UNPIPELINED 0x20u /* FP32 TTMc without the one-tile-ahead register prefetch
                                       (same arithmetic, kept for comparison) */
 

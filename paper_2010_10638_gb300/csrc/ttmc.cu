@@ -913,30 +913,10 @@ void fill_iota_ones(uint32_t *iota, float *ones, int64_t n, cudaStream_t s) {
 // ============================================================================ tensor-core form
 // The contribution of one slice is the small GEMM  Y_i (PL x RB) = A_i^T B_i  with
 // A_i = [x_z a_z] and B_i = [b_z] over its nonzeros z (K = slice length).  PL = 16 k
-// rows fit the m16n8 tiles of mma.sync exactly (tcgen05 needs M >= 64), so a warp
-// runs the slice segments of its tile through mma.sync with K = the segment's
-// nonzeros (rows outside the segment masked to zero):
-//   kTf32x3  FP32 form: a = a_hi + a_lo, b = b_hi + b_lo (TF32 parts), three
-//            m16n8k8 products hi*hi + hi*lo + lo*hi, FP32 accumulation
-//   kBf16    BF16-factor form: one m16n8k16 BF16 product, FP32 accumulation
-// Accumulators stay in the MMA C fragments while a segment continues across tiles.
-enum MmaMode { kTf32x3 = 0, kBf16 = 1 };
-
-__device__ __forceinline__ uint32_t tf32_of(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
-__device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo) {
-  hi = tf32_of(x);
-  lo = tf32_of(x - __uint_as_float(hi));
-}
-__device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
+// rows fit the m16n8 tiles of mma.sync exactly, so a warp runs the slice segments of its
+// tile through m16n8k16 BF16 products with K = the segment's nonzeros (rows outside the
+// segment masked to zero), FP32 accumulation: the BF16-factor form.  Accumulators stay in
+// the MMA C fragments while a segment continues across tiles.
 __device__ __forceinline__ uint32_t pack_bf16(float lo_k, float hi_k) {
   uint32_t r;  // lower 16 bits hold the element with the lower k index
   asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi_k), "f"(lo_k));
@@ -948,8 +928,6 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], 
       : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
-
-__host__ __device__ constexpr int stride_mod32_8(int v) { return v + ((8 - (v % 32)) % 32 + 32) % 32; }
 
 // BF16-factor form with ldmatrix fragments.  Staging (lane = nonzero of the tile): the
 // left Kronecker row times x_z is formed in FP32 from the BF16 factor rows and rounded to
@@ -1369,165 +1347,6 @@ __global__ void __launch_bounds__(kTmaWarps * 32) ttmc_bf16_tma_kernel(const Ttm
   }
 }
 
-template <int NL, int PL, int RB, int MODE, typename FT>
-__global__ void __launch_bounds__(kTtmcWarps * 32) ttmc_mma_kernel(const TtmcParams p) {
-  static_assert(PL % 16 == 0 && RB % 8 == 0, "mma tiles");
-  constexpr int MT = PL / 16, NT = RB / 8;
-  constexpr int SA = stride_mod32_8(PL);  // shared row strides = 8 (mod 32): conflict-free fragment loads
-  constexpr int SB = stride_mod32_8(RB);
-  constexpr int KS = (MODE == kTf32x3) ? 8 : 16;  // nonzeros per MMA k-step
-  extern __shared__ float4 smem_f4[];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  float *xa = reinterpret_cast<float *>(smem_f4) + w * (32 + KS) * (SA + SB);
-  float *bb = xa + (32 + KS) * SA;
-  const int64_t u = (int64_t)blockIdx.x * kTtmcWarps + w;
-  if (u >= p.n_units) return;
-  const FT *UB = static_cast<const FT *>(p.U[NL]);
-  const uint32_t *idxB = p.idx[NL];
-  uint32_t e = __ldg(p.unit_e0 + u);
-  const uint32_t e_end = (u + 1 < p.n_units) ? __ldg(p.unit_e0 + u + 1) : p.Z;
-  uint32_t kb = __ldg(p.unit_k0 + u);
-  const int slot = __ldg(p.unit_slot + u);
-  const int g = lane >> 2, t = lane & 3;
-  float acc[MT][NT][4];
-#pragma unroll
-  for (int i = 0; i < MT; ++i)
-#pragma unroll
-    for (int j = 0; j < NT; ++j)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
-  // rows 32 .. 32+KS-1 of the staging buffers stay zero: k-steps may run past the tile
-  for (int q = lane; q < KS * SA; q += 32) xa[32 * SA + q] = 0.f;
-  for (int q = lane; q < KS * SB; q += 32) bb[32 * SB + q] = 0.f;
-
-  while (e < e_end) {
-    const int nt = (int)min(32u, e_end - e);
-    const TileSlices ts = tile_slices(p.sptr, p.S, kb, e, nt, lane);
-    float x = 0.f;
-    uint32_t i0 = 0, i1 = 0, ib = 0;
-    if (lane < nt) {
-      x = __ldg(p.val + e + lane);
-      ib = __ldg(idxB + e + lane);
-      if constexpr (NL >= 1) i0 = __ldg(p.idx[0] + e + lane);
-      if constexpr (NL >= 2) i1 = __ldg(p.idx[1] + e + lane);
-    }
-    __syncwarp();
-    if constexpr (NL == 1) {
-      const FT *U0 = static_cast<const FT *>(p.U[0]);
-#pragma unroll
-      for (int it = lane; it < 32 * (PL / 4); it += 32) {
-        const int tt = it / (PL / 4), c = (it % (PL / 4)) * 4;
-        const float xt = __shfl_sync(kFull, x, tt);
-        const uint32_t r = __shfl_sync(kFull, i0, tt);
-        float4 v = Ld<FT>::v4(U0 + (size_t)r * PL, c);
-        v.x *= xt;
-        v.y *= xt;
-        v.z *= xt;
-        v.w *= xt;
-        *reinterpret_cast<float4 *>(xa + tt * SA + c) = v;
-      }
-    } else {
-      const FT *U0 = static_cast<const FT *>(p.U[0]);
-      const FT *U1 = static_cast<const FT *>(p.U[1]);
-      const int R1 = p.R[1], R0 = p.R[0];
-#pragma unroll 4
-      for (int it = lane; it < 32 * (PL / 4); it += 32) {
-        const int tt = it / (PL / 4), c = (it % (PL / 4)) * 4;
-        const float xt = __shfl_sync(kFull, x, tt);
-        const uint32_t r0 = __shfl_sync(kFull, i0, tt);
-        const uint32_t r1 = __shfl_sync(kFull, i1, tt);
-        const int a0 = c / R1, a1 = c - a0 * R1;
-        const float s0 = xt * Ld<FT>::s(U0 + (size_t)r0 * R0, a0);
-        float4 v = Ld<FT>::v4(U1 + (size_t)r1 * R1, a1);
-        v.x *= s0;
-        v.y *= s0;
-        v.z *= s0;
-        v.w *= s0;
-        *reinterpret_cast<float4 *>(xa + tt * SA + c) = v;
-      }
-    }
-#pragma unroll
-    for (int it = lane; it < 32 * (RB / 4); it += 32) {
-      const int tt = it / (RB / 4), c = (it % (RB / 4)) * 4;
-      const uint32_t r = __shfl_sync(kFull, ib, tt);
-      *reinterpret_cast<float4 *>(bb + tt * SB + c) = Ld<FT>::v4(UB + (size_t)r * RB, c);
-    }
-    __syncwarp();
-
-    uint32_t segs = ts.starts | 1u;
-    while (segs) {
-      const int p0 = __ffs(segs) - 1;
-      segs &= segs - 1u;
-      const int p1 = segs ? (__ffs(segs) - 1) : nt;
-      for (int k0 = p0; k0 < p1; k0 += KS) {
-        if constexpr (MODE == kTf32x3) {
-          const int ka = k0 + t, kb2 = k0 + t + 4;
-          const bool va = ka < p1, vb = kb2 < p1;
-#pragma unroll
-          for (int mt = 0; mt < MT; ++mt) {
-            const int m = mt * 16 + g;
-            const float f0 = va ? xa[ka * SA + m] : 0.f;
-            const float f1 = va ? xa[ka * SA + m + 8] : 0.f;
-            const float f2 = vb ? xa[kb2 * SA + m] : 0.f;
-            const float f3 = vb ? xa[kb2 * SA + m + 8] : 0.f;
-            uint32_t ahi[4], alo[4];
-            split_tf32(f0, ahi[0], alo[0]);
-            split_tf32(f1, ahi[1], alo[1]);
-            split_tf32(f2, ahi[2], alo[2]);
-            split_tf32(f3, ahi[3], alo[3]);
-#pragma unroll
-            for (int nq = 0; nq < NT; ++nq) {
-              const int n = nq * 8 + g;
-              uint32_t b0h, b0l, b1h, b1l;
-              split_tf32(bb[ka * SB + n], b0h, b0l);
-              split_tf32(bb[kb2 * SB + n], b1h, b1l);
-              mma_tf32(acc[mt][nq], alo, b0h, b1h);
-              mma_tf32(acc[mt][nq], ahi, b0l, b1l);
-              mma_tf32(acc[mt][nq], ahi, b0h, b1h);
-            }
-          }
-        } else {
-          const int ka = k0 + 2 * t, kc = k0 + 2 * t + 8;
-#pragma unroll
-          for (int mt = 0; mt < MT; ++mt) {
-            const int m = mt * 16 + g;
-            uint32_t a[4];
-            a[0] = pack_bf16(ka < p1 ? xa[ka * SA + m] : 0.f, ka + 1 < p1 ? xa[(ka + 1) * SA + m] : 0.f);
-            a[1] = pack_bf16(ka < p1 ? xa[ka * SA + m + 8] : 0.f, ka + 1 < p1 ? xa[(ka + 1) * SA + m + 8] : 0.f);
-            a[2] = pack_bf16(kc < p1 ? xa[kc * SA + m] : 0.f, kc + 1 < p1 ? xa[(kc + 1) * SA + m] : 0.f);
-            a[3] = pack_bf16(kc < p1 ? xa[kc * SA + m + 8] : 0.f, kc + 1 < p1 ? xa[(kc + 1) * SA + m + 8] : 0.f);
-#pragma unroll
-            for (int nq = 0; nq < NT; ++nq) {
-              const int n = nq * 8 + g;
-              const uint32_t b0 = pack_bf16(bb[ka * SB + n], bb[(ka + 1) * SB + n]);
-              const uint32_t b1 = pack_bf16(bb[kc * SB + n], bb[(kc + 1) * SB + n]);
-              mma_bf16(acc[mt][nq], a, b0, b1);
-            }
-          }
-        }
-      }
-      const bool flush = (p1 < nt) || ts.end_is_start || (e + (uint32_t)nt == e_end);
-      if (flush) {
-        const uint32_t kseg = __shfl_sync(kFull, ts.kp, p0);
-        float *dst = (slot >= 0) ? p.carry + (size_t)slot * p.P : p.Y + (size_t)__ldg(p.sid + kseg) * p.P;
-#pragma unroll
-        for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-          for (int nq = 0; nq < NT; ++nq) {
-            const int row = mt * 16 + g, col = nq * 8 + 2 * t;
-            *reinterpret_cast<float2 *>(dst + (size_t)row * RB + col) = make_float2(acc[mt][nq][0], acc[mt][nq][1]);
-            *reinterpret_cast<float2 *>(dst + (size_t)(row + 8) * RB + col) =
-                make_float2(acc[mt][nq][2], acc[mt][nq][3]);
-            acc[mt][nq][0] = acc[mt][nq][1] = acc[mt][nq][2] = acc[mt][nq][3] = 0.f;
-          }
-      }
-    }
-    kb = ts.kb_next;
-    e += (uint32_t)nt;
-    __syncwarp();
-  }
-}
-
 // Any shape: each lane owns CPL columns of a block of 32*CPL columns (grid.y), and
 // forms its Kronecker entries directly from the factor rows (cached loads).
 template <int CPL, typename FT>
@@ -1703,32 +1522,14 @@ static bool tma_rows() {
   return e && e[0] == '1';
 }
 
-template <int NL, int PL, int RB, int MODE, typename FT>
-static cudaError_t run_mma(const TtmcParams &p, cudaStream_t s) {
-  if constexpr (MODE == kBf16) return run_bf16<NL, PL, RB>(p, s);
-  constexpr int KS = (MODE == kTf32x3) ? 8 : 16;
-  const size_t smem =
-      (size_t)kTtmcWarps * (32 + KS) * (stride_mod32_8(PL) + stride_mod32_8(RB)) * sizeof(float);
-  auto kern = ttmc_mma_kernel<NL, PL, RB, MODE, FT>;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  const unsigned blocks = (unsigned)((p.n_units + kTtmcWarps - 1) / kTtmcWarps);
-  kern<<<blocks, kTtmcWarps * 32, smem, s>>>(p);
-  ::tk::count_launch();
-  return cudaGetLastError();
-}
-
-// Tensor-core dispatch (shapes with PL % 16 == 0 and RB % 8 == 0).
-template <int MODE, typename FT>
-static bool dispatch_mma(const TtmcParams &p, cudaStream_t s, cudaError_t *err) {
+// BF16-factor dispatch (shapes with PL % 16 == 0 and RB % 8 == 0).
+static bool dispatch_bf16(const TtmcParams &p, cudaStream_t s, cudaError_t *err) {
   const int no = p.nother;
   const int RB = p.R[no - 1];
-#define TK_MMA(NL_, PL_, RB_)                              \
-  {                                                        \
-    *err = run_mma<NL_, PL_, RB_, MODE, FT>(p, s);         \
-    return true;                                           \
+#define TK_MMA(NL_, PL_, RB_)                \
+  {                                          \
+    *err = run_bf16<NL_, PL_, RB_>(p, s);    \
+    return true;                             \
   }
   if (no == 2) {
     const int PL = p.R[0];
@@ -1888,7 +1689,7 @@ static tucker_status ttmc_impl(Ctx *c, int mode, float *Y, const float *val, con
   p.P = mc.P;
   p.err = c->d_err;
   // A fiber level, opt-in fused kernel (fiber sums kept on chip), FP32 or BF16 factors
-  if (!(c->flags & (TUCKER_F_TF32X3 | TUCKER_F_UNPIPELINED)) && mc.fib && mc.n_units > 0 && mc.unit_f0 &&
+  if (!(c->flags & TUCKER_F_UNPIPELINED) && mc.fib && mc.n_units > 0 && mc.unit_f0 &&
       p.nother == 2 && fused_fibers()) {
     const int ft = mc.fmid_t;
     FiberParams f{};
@@ -1929,7 +1730,7 @@ static tucker_status ttmc_impl(Ctx *c, int mode, float *Y, const float *val, con
   }
   // FP32 factors with a fiber level, two passes: fiber sums to HBM, then the pipelined
   // update over fibers
-  if (!bf16 && !(c->flags & (TUCKER_F_TF32X3 | TUCKER_F_UNPIPELINED)) && mc.fib && mc.fn_units > 0 && c->fib_T &&
+  if (!bf16 && !(c->flags & TUCKER_F_UNPIPELINED) && mc.fib && mc.fn_units > 0 && c->fib_T &&
       p.nother == 2 && pipe_shape(p.R[0], p.R[1])) {
     TtmcParams q = p;
     q.sptr = mc.fsptr;
@@ -1974,11 +1775,9 @@ static tucker_status ttmc_impl(Ctx *c, int mode, float *Y, const float *val, con
         err = run_bf16_tma<16, 16>(p, c->tm16[mc.other[0]], c->tm16[mc.other[1]], s);
         done = true;
       } else {
-        done = dispatch_mma<kBf16, __nv_bfloat16>(p, s, &err);
+        done = dispatch_bf16(p, s, &err);
       }
-    } else if (c->flags & TUCKER_F_TF32X3)  // opt-in FP32-class form on the tensor cores
-      done = dispatch_mma<kTf32x3, float>(p, s, &err);
-    else if (!(c->flags & TUCKER_F_UNPIPELINED))
+    } else if (!(c->flags & TUCKER_F_UNPIPELINED))
       done = dispatch_pipe(p, s, &err);
     if (!done) done = bf16 ? dispatch_fast<__nv_bfloat16>(p, s, &err) : dispatch_fast<float>(p, s, &err);
     if (!done) err = bf16 ? run_generic<__nv_bfloat16>(p, s) : run_generic<float>(p, s);

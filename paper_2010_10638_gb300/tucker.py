@@ -27,7 +27,6 @@ TUCKER_F_BF16_FACTORS = 0x1
 TUCKER_F_QRP_DIRECT = 0x2
 TUCKER_F_HOST_INPUT = 0x4
 TUCKER_F_FIT_DEVICE = 0x8
-TUCKER_F_TF32X3 = 0x10
 TUCKER_F_UNPIPELINED = 0x20
 
 STATUS = {0: "TUCKER_OK", 1: "TUCKER_EINVAL", 2: "TUCKER_ERANK", 3: "TUCKER_ENOMEM", 4: "TUCKER_ECUDA",
@@ -160,7 +159,7 @@ class Context:
 
 # --------------------------------------------------------------------------- entry points
 def tucker_init(dims, coords, vals, ranks, U0=None, seed: int = 0, bf16: bool = False, direct: bool = False,
-                fit_device: bool = False, tf32x3: bool = False, unpipelined: bool = False,
+                fit_device: bool = False, unpipelined: bool = False,
                 stream=None) -> Context:
     """coords: int32/uint32 [N, nnz]; vals: float32 [nnz]; U0: list of N float64 [I_m, R_m] or None.
     CUDA tensors are passed as device pointers; CPU tensors / numpy arrays as host pointers
@@ -168,7 +167,7 @@ def tucker_init(dims, coords, vals, ranks, U0=None, seed: int = 0, bf16: bool = 
     lib = load()
     N = len(dims)
     flags = (TUCKER_F_BF16_FACTORS if bf16 else 0) | (TUCKER_F_QRP_DIRECT if direct else 0) | (
-        TUCKER_F_FIT_DEVICE if fit_device else 0) | (TUCKER_F_TF32X3 if tf32x3 else 0) | (
+        TUCKER_F_FIT_DEVICE if fit_device else 0) | (
         TUCKER_F_UNPIPELINED if unpipelined else 0)
     on_host = not (isinstance(coords, torch.Tensor) and coords.is_cuda)
     keep = []
