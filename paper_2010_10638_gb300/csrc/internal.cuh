@@ -168,6 +168,28 @@ void reset_alloc_counter();
 size_t scan_tmp_elems(int64_t n);
 void exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *tmp, cudaStream_t s);
 
+// ---- stable LSD radix sort of records of 32-bit words (radix.cu)
+constexpr int kRadixMaxWords = kMaxOrder + 3;
+struct RadixRecords {
+  int nwords = 0;
+  const uint32_t *in[kRadixMaxWords] = {};  // nullptr: the word is the record's input position
+  uint32_t *out[kRadixMaxWords] = {};       // sorted words; must not alias `in`
+};
+struct RadixKey {
+  int word;  // key word (least significant key first in the key list)
+  int bits;  // its values are < 2^bits
+};
+int radix_bits(int64_t maxval);  // bits needed for values 0..maxval
+size_t radix_scratch_bytes(int64_t n, int nwords, const RadixKey *keys, int nkeys);
+// Sorts the n records by keys[nkeys-1], ..., keys[0] (most significant last), stable.
+// Optionally validates words 0..nvalid-1 against valid_dims (device) and valid_vals for
+// finiteness, setting bits of *err.  A look-back wait that gives up sets kErrTimeout.
+// Returns 0, -1 (bad arguments) or -2 (a CUDA call failed).
+int radix_sort_records(int64_t n, const RadixRecords &r, const RadixKey *keys, int nkeys, const int64_t *valid_dims,
+                       int nvalid, const float *valid_vals, void *scratch, size_t scratch_bytes, uint32_t *err,
+                       cudaStream_t s);
+void iota_u32(uint32_t *out, int64_t n, cudaStream_t s);
+
 // ---- K-a: reorder (reorder.cu)
 tucker_status build_sorted_copies(Ctx *c, const uint32_t *coords, const float *vals, cudaStream_t s);
 

@@ -183,8 +183,13 @@ def tucker_init(dims, coords, vals, ranks, U0=None, seed: int = 0, bf16: bool = 
         c = coords if coords.dtype == torch.int32 else coords.to(torch.int32)
         c = _dev(c.contiguous(), torch.int32, "coords")
         v = _dev(vals.contiguous(), torch.float32, "vals")
-        if U0 is not None:
-            u = torch.cat([_dev(x.contiguous(), torch.float64, "U0").reshape(-1) for x in U0])
+        if U0 is not None:  # one buffer, filled by device-to-device copies
+            parts = [_dev(x.contiguous(), torch.float64, "U0").reshape(-1) for x in U0]
+            u = torch.empty(sum(int(p.numel()) for p in parts), dtype=torch.float64, device=parts[0].device)
+            off = 0
+            for p in parts:
+                u[off:off + p.numel()].copy_(p)
+                off += p.numel()
     nnz = int(v.numel())
     if tuple(c.shape) != (N, nnz):
         raise ValueError(f"coords must have shape ({N}, {nnz}), got {tuple(c.shape)}")
