@@ -4,14 +4,18 @@
 // Kronecker accumulation of Algorithm 2 over its nonzeros.  On the GPU every mode gets
 // its own copy of the nonzeros sorted by that mode's index, so that the nonzeros of a
 // slice (one row of Y_(n)) are contiguous and can be reduced without atomics:
-//   - LSD radix passes (8-bit digits, stable: histogram -> exclusive scan -> scatter
-//     ranked with warp match) sort by the full coordinate, mode 1 most significant;
+//   - a stable radix sort of whole records (radix.cu) by the full coordinate, mode 1 most
+//     significant, validating every coordinate and value on the way;
 //   - equal neighbours are summed in FP64 (input order) into one nonzero;
-//   - per mode: stable radix sort by i_n, gather of the other modes' indices and the
-//     values (structure of arrays), offsets of the non-empty slices (a CSF root
-//     level), the list of empty rows, and a table of work units of about `chunk`
-//     nonzeros: runs of whole short slices, or pieces of a long slice whose partial
-//     rows are combined by a second pass.
+//   - per mode: a stable radix sort of the coalesced records by i_n (the other modes'
+//     indices, the value and the source position carried: structure of arrays), offsets
+//     of the non-empty slices (a CSF root level), the list of empty rows, and a table of
+//     work units of about `chunk` nonzeros: runs of whole short slices, or pieces of a
+//     long slice whose partial rows are combined by a second pass;
+//   - order 3: a fiber level (runs of one slice with one middle index, cut every
+//     kFiberCap nonzeros) where fibers are few enough to pay.
+// Positions where something starts (a group, a slice, a run) are numbered by per-tile
+// counts, one block's prefix over the tiles, and a pass that writes the compacted lists.
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
