@@ -60,6 +60,18 @@ typedef enum {
                                       (same arithmetic, kept for comparison) */
 
 /*
+ * tucker_lib_setup — optional one-time set-up of the library on a device: creates the
+ * library's stream-ordered memory pool, makes its first allocation (a process's first use
+ * of the stream-ordered allocator costs milliseconds), and loads the kernels that
+ * tucker_init launches (under lazy module loading they would load at their first launch).
+ * Without it the same happens on first use.  Safe to call again; leaves the calling
+ * thread's current device unchanged.
+ *   device  CUDA device ordinal
+ * Returns TUCKER_OK, or TUCKER_ECUDA (no such device, or a CUDA call failed).
+ */
+TUCKER_API tucker_status tucker_lib_setup(int device);
+
+/*
  * tucker_init — load a sparse tensor and prepare it for HOOI (Algorithm 2 input:
  * the sparse tensor X and the ranks R_1..R_N; COO storage, Section III-A).
  *
@@ -84,8 +96,10 @@ typedef enum {
  * is taken over the summed values.  For every mode the context builds a copy of the
  * nonzeros sorted by that mode's index (stable), the offsets of each non-empty
  * slice, and a table of work units of near-equal nonzero count.
- * Synchronises `stream` once (the coalesced count sizes the copies) and returns
- * TUCKER_EINVAL for a coordinate >= I_m or a non-finite value.
+ * Synchronises `stream` a few times (counts read back size the copies: the coalesced
+ * nonzeros, then each mode's slices, units and fibers) and returns TUCKER_EINVAL for a
+ * coordinate >= I_m or a non-finite value, TUCKER_ETIMEOUT if a bounded device-side wait
+ * of the sort gave up (the context is not created).
  */
 TUCKER_API tucker_status tucker_init(tucker_ctx **out, int order, const int64_t *dims, int64_t nnz,
                           const uint32_t *coords, const float *vals, const int *ranks,

@@ -415,6 +415,32 @@ tucker_status tucker_selftest_wait(tucker_ctx *h, uint64_t max_polls, void *stre
   return tk::launch_wait_selftest(&h->c, (unsigned long long)max_polls, static_cast<cudaStream_t>(stream));
 }
 
+tucker_status tucker_lib_setup(int device) {
+  int old = 0, count = 0;
+  if (cudaGetDevice(&old) != cudaSuccess || cudaGetDeviceCount(&count) != cudaSuccess) {
+    cudaGetLastError();
+    return TUCKER_ECUDA;
+  }
+  if (device < 0 || device >= count || cudaSetDevice(device) != cudaSuccess) {
+    cudaGetLastError();
+    return TUCKER_ECUDA;
+  }
+  cudaError_t e = tk::pool_warm(device);
+  if (e == cudaSuccess) e = tk::preload_radix_kernels();
+  if (e == cudaSuccess) e = tk::preload_reorder_kernels();
+  if (e == cudaSuccess) e = tk::preload_ttmc_init_kernels();
+  if (e == cudaSuccess) {
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, tk::f64_to_f32_kernel);
+  }
+  cudaSetDevice(old);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return TUCKER_ECUDA;
+  }
+  return TUCKER_OK;
+}
+
 tucker_status tucker_init(tucker_ctx **out, int order, const int64_t *dims, int64_t nnz, const uint32_t *coords,
                           const float *vals, const int *ranks, const double *U0, uint64_t seed, uint32_t flags,
                           void *stream) {

@@ -43,8 +43,8 @@ struct ModeCopy {
   uint32_t *long_u0 = nullptr;         // [n_long] their first unit (= first partial slot)
   uint32_t *long_np = nullptr;         // [n_long] their number of units
   int64_t n_long = 0;
-  uint32_t *src = nullptr;             // [nnz] coalesced (lexicographic) index of sorted position e;
-                                       // nullptr for mode 1, whose order is the lexicographic one
+  uint32_t *src = nullptr;             // [nnz] index in the coalesced order of sorted position e;
+                                       // nullptr for a mode 1 copy in the coalesced order itself
   // Fiber level (order 3): within a slice, runs of nonzeros with the same index of the
   // middle remaining mode other[fmid_t], cut every kFiberCap nonzeros (with fmid_t = 1 the
   // copy is sorted by (i_n, i_other[1], i_other[0])).  Work units and long-slice tables over
@@ -99,7 +99,7 @@ struct Ctx {
   int num_sms = 0;
   int device = 0;
 
-  uint32_t *coords = nullptr;  // coalesced [N][nnz] (lexicographic order)
+  uint32_t *coords = nullptr;  // coalesced [N][nnz], sorted by the full key (mode 1 first)
   float *vals = nullptr;       // coalesced values (FP32 rounding of the FP64 sums)
   ModeCopy mode[kMaxOrder];
 
@@ -192,6 +192,12 @@ void iota_u32(uint32_t *out, int64_t n, cudaStream_t s);
 
 // ---- K-a: reorder (reorder.cu)
 tucker_status build_sorted_copies(Ctx *c, const uint32_t *coords, const float *vals, cudaStream_t s);
+// the library pool of `device` with one allocation made and freed (current device = device)
+cudaError_t pool_warm(int device);
+// load the kernels the initialisation launches (cudaFuncGetAttributes on each)
+cudaError_t preload_radix_kernels();
+cudaError_t preload_reorder_kernels();
+cudaError_t preload_ttmc_init_kernels();
 
 // ---- K-b: TTMc (ttmc.cu)
 tucker_status launch_ttmc(Ctx *c, int mode, float *Y, cudaStream_t s);

@@ -484,6 +484,14 @@ __global__ void rx_iota_kernel(uint32_t *out, int64_t n) {
     out[e] = (uint32_t)e;
 }
 
+cudaError_t preload_radix_kernels() {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, rx_hist_kernel);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, rx_pass_kernel);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, rx_iota_kernel);
+  return e;
+}
+
 void iota_u32(uint32_t *out, int64_t n, cudaStream_t s) {
   if (n <= 0) return;
   rx_iota_kernel<<<(unsigned)std::min<int64_t>(rx_cdiv(n, 256), 65535LL * 8), 256, 0, s>>>(out, n);

@@ -78,6 +78,21 @@ cudaError_t dev_alloc(Ctx *c, void **p, size_t bytes) {
   return e;
 }
 
+cudaError_t pool_warm(int device) {
+  cudaMemPool_t pool = nullptr;
+  cudaError_t e = pool_for(device, &pool);
+  if (e != cudaSuccess) return e;
+  cudaStream_t s = nullptr;
+  e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return e;
+  void *p = nullptr;
+  e = cudaMallocFromPoolAsync(&p, 1 << 20, pool, s);
+  if (e == cudaSuccess) e = cudaFreeAsync(p, s);
+  const cudaError_t e2 = cudaStreamSynchronize(s);
+  cudaStreamDestroy(s);
+  return e != cudaSuccess ? e : e2;
+}
+
 // frees p (one of c's allocations) in the order of c->astream
 void dev_free(Ctx *c, void *p) {
   if (!p) return;
@@ -726,6 +741,36 @@ static int fiber_policy() {
   return -1;
 }
 constexpr double kFiberShare = 0.25;
+
+cudaError_t preload_reorder_kernels() {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaSuccess;
+  const void *k[] = {
+      reinterpret_cast<const void *>(scan_block_kernel),
+      reinterpret_cast<const void *>(scan_add_kernel),
+      reinterpret_cast<const void *>(tile_count_kernel),
+      reinterpret_cast<const void *>(tile_prefix_kernel),
+      reinterpret_cast<const void *>(tile_compact_kernel<SliceWrite>),
+      reinterpret_cast<const void *>(tile_compact_kernel<StartWrite>),
+      reinterpret_cast<const void *>(coalesce_write_kernel),
+      reinterpret_cast<const void *>(reduce_f64_final),
+      reinterpret_cast<const void *>(invert_flag_kernel),
+      reinterpret_cast<const void *>(compact_kernel),
+      reinterpret_cast<const void *>(slice_count_kernel),
+      reinterpret_cast<const void *>(slice_bits_kernel),
+      reinterpret_cast<const void *>(run_pieces_kernel),
+      reinterpret_cast<const void *>(fiber_emit_kernel),
+      reinterpret_cast<const void *>(fiber_emit_long_kernel),
+      reinterpret_cast<const void *>(fiber_slices_kernel),
+      reinterpret_cast<const void *>(unit_fiber_kernel),
+      reinterpret_cast<const void *>(unit_count_kernel),
+      reinterpret_cast<const void *>(unit_write_kernel),
+      reinterpret_cast<const void *>(unit_long_kernel),
+  };
+  for (const void *f : k)
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, f);
+  return e;
+}
 
 // Reads a device total and the error word in one synchronisation; a set error bit ends the
 // initialisation (the sorted words may be wrong and must not be used as indices).

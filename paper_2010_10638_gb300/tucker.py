@@ -37,7 +37,7 @@ EXPORTS = ["tucker_init", "ttmc_mode", "qrp_leading", "qrp_leading_work_bytes", 
            "tucker_sync_status", "tucker_free", "tucker_status_str", "tucker_last_error", "tucker_set_profiling",
            "tucker_phase_times", "tucker_kernel_launches", "qrp_leading_noalloc", "qrp_leading_noalloc_max_bytes",
            "tucker_selftest_wait", "tucker_mode_info", "qrp_leading_sync_status",
-           "qrp_leading_noalloc_sync_status", "tucker_fp32_fma_tflops", "tucker_hooi_graph"]
+           "qrp_leading_noalloc_sync_status", "tucker_fp32_fma_tflops", "tucker_hooi_graph", "tucker_lib_setup"]
 
 
 class TuckerError(RuntimeError):
@@ -102,6 +102,8 @@ def load(path: str = LIB_PATH):
     lib.tucker_fp32_fma_tflops.restype = dbl
     lib.tucker_mode_info.argtypes = [vp, cint, P(i64), cint]
     lib.tucker_mode_info.restype = cint
+    lib.tucker_lib_setup.argtypes = [cint]
+    lib.tucker_lib_setup.restype = cint
     lib.tucker_kernel_launches.argtypes = []
     lib.tucker_kernel_launches.restype = ctypes.c_uint64
     for name in ("tucker_init", "ttmc_mode", "qrp_leading", "hooi_iter", "core_tensor", "tucker_get_factor",
@@ -158,6 +160,14 @@ class Context:
 
 
 # --------------------------------------------------------------------------- entry points
+def tucker_lib_setup(device: int | None = None) -> None:
+    """One-time set-up of the library on a device (memory pool, first allocation, the
+    initialisation's kernels); optional, otherwise done on first use."""
+    lib = load()
+    dev = torch.cuda.current_device() if device is None else int(device)
+    _check(lib.tucker_lib_setup(dev), "tucker_lib_setup")
+
+
 def tucker_init(dims, coords, vals, ranks, U0=None, seed: int = 0, bf16: bool = False, direct: bool = False,
                 fit_device: bool = False, unpipelined: bool = False,
                 stream=None) -> Context:

@@ -194,3 +194,57 @@ def test_bounded_wait_times_out_and_context_survives():
     Y = T.ttmc_mode(ctx, 0)
     assert torch.isfinite(Y).all()
     assert 0.0 < T.hooi_iter(ctx) < 1.0
+
+
+@pytest.mark.parametrize("dims", [(3, 1 << 17, 7), (5, (1 << 24) + 3, 2), (1, 40, 30), (20, 1, 1)],
+                         ids=["17-bit", "25-bit", "one-row-mode1", "one-row-modes23"])
+def test_sort_key_widths(dims):
+    """Indices of 17 and 25 bits (three and four sort passes of under 8 bits each) and
+    modes with a single index (no pass): the mode copies, hence Y, against the oracle."""
+    rng = np.random.default_rng(sum(dims))
+    nnz = 30_011
+    coords = np.stack([rng.integers(0, d, nnz) for d in dims]).astype(np.uint32)
+    vals = rng.standard_normal(nnz).astype(np.float32)
+    ranks = tuple(min(2, d) for d in dims)
+    U = synth.random_factors(rng, dims, ranks)
+    _, Ys = run_ttmc_all_modes(dims, ranks, coords, vals, U)
+    ref = oracle_all_modes(dims, ranks, coords, vals, U)
+    for n in range(3):
+        assert rel_fro(Ys[n], ref[n]) <= TOL, f"mode {n}"
+
+
+def test_duplicate_groups_across_warp_and_tile_edges():
+    """Groups of equal coordinates that straddle 32-position steps, 512-position warps and
+    8192-position tiles of the coalescing pass (one group of 20,000 copies), summed in FP64."""
+    T = lib()
+    rng = np.random.default_rng(41)
+    dims, ranks = (64, 48, 40), (4, 4, 4)
+    base = np.stack([rng.integers(0, d, 30_000) for d in dims]).astype(np.uint32)
+    reps = rng.integers(1, 70, base.shape[1])
+    coords = np.repeat(base, reps, axis=1)
+    big = np.repeat(np.array([[5], [7], [9]], dtype=np.uint32), 20_000, axis=1)
+    coords = np.concatenate([coords, big], axis=1)
+    perm = rng.permutation(coords.shape[1])
+    coords = coords[:, perm]
+    vals = rng.standard_normal(coords.shape[1]).astype(np.float32)
+    U = synth.random_factors(rng, dims, ranks)
+    ctx, Ys = run_ttmc_all_modes(dims, ranks, coords, vals, U)
+    cc, cv = oracle.coalesce(coords, vals.astype(np.float64))
+    assert T.tucker_nnz(ctx) == cc.shape[1]
+    assert T.tucker_norm2(ctx) == pytest.approx(oracle.norm2(cv), rel=1e-12)
+    ref = oracle_all_modes(dims, ranks, coords, vals, U)
+    for n in range(3):
+        assert rel_fro(Ys[n], ref[n]) <= TOL, f"mode {n}"
+
+
+def test_lib_setup():
+    T = lib()
+    T.tucker_lib_setup()
+    T.tucker_lib_setup()  # again: no effect
+    with pytest.raises(T.TuckerError) as e:
+        T.tucker_lib_setup(torch.cuda.device_count() + 3)
+    assert e.value.name == "TUCKER_ECUDA"
+    assert torch.cuda.current_device() == 0
+    w = synth.make("tiny-100^3")
+    ctx = T.tucker_init(w.workload.dims, w.coords, w.vals, w.workload.ranks, w.U0)
+    assert T.tucker_nnz(ctx) == w.workload.nnz

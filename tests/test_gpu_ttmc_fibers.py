@@ -107,3 +107,31 @@ def test_fiber_form_in_the_adjoint(monkeypatch, dims):
     assert rel_fro(dG, dGr) <= 1e-4
     for n in range(3):
         assert rel_fro(dU[n], dUr[n]) <= 1e-4, f"mode {n}"
+
+
+@pytest.mark.parametrize("mid", [1, 2], ids=["middle-mode2", "middle-mode3"])
+def test_mode1_middle_level_against_the_size_guess(mid, monkeypatch):
+    """Mode 1's copy is first ordered with its smaller remaining mode as the middle level; when
+    the other remaining mode has far fewer distinct (i_1, i_m) pairs the copy is re-sorted from
+    that mode's copy.  Here the dimensions point one way and the pairs the other."""
+    monkeypatch.setenv("TUCKER_TTMC_FIBERS", "1")
+    rng = np.random.default_rng(31 + mid)
+    nnz = 40_003
+    i1 = rng.integers(0, 100, nnz)
+    if mid == 2:  # mode 3 (dim 50) repeats per i_1, mode 2 (dim 40) is the smaller one
+        dims = (100, 40, 50)
+        coords = np.stack([i1, rng.integers(0, 40, nnz), (i1 * 7 + rng.integers(0, 2, nnz)) % 50])
+    else:  # mode 2 (dim 50) repeats per i_1, mode 3 (dim 40) is the smaller one
+        dims = (100, 50, 40)
+        coords = np.stack([i1, (i1 * 3 + rng.integers(0, 2, nnz)) % 50, rng.integers(0, 40, nnz)])
+    coords = coords.astype(np.uint32)
+    ranks = (8, 8, 8)
+    vals = rng.standard_normal(nnz).astype(np.float32)
+    U = synth.random_factors(rng, dims, ranks)
+    ctx, Ys = run_ttmc_all_modes(dims, ranks, coords, vals, U)
+    from tests.gpu_util import lib
+    info = lib().tucker_mode_info(ctx, 0)
+    assert info["fibers_on"] == 1 and info["fiber_mid_mode"] == mid
+    ref = oracle_all_modes(dims, ranks, coords, vals, U)
+    for n in range(3):
+        assert rel_fro(Ys[n], ref[n]) <= TOL, f"mode {n}"
