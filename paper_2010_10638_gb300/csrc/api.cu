@@ -428,7 +428,6 @@ tucker_status tucker_lib_setup(int device) {
   cudaError_t e = tk::pool_warm(device);
   if (e == cudaSuccess) e = tk::preload_radix_kernels();
   if (e == cudaSuccess) e = tk::preload_reorder_kernels();
-  if (e == cudaSuccess) e = tk::preload_ttmc_init_kernels();
   if (e == cudaSuccess) {
     cudaFuncAttributes fa;
     e = cudaFuncGetAttributes(&fa, tk::f64_to_f32_kernel);

@@ -197,7 +197,6 @@ cudaError_t pool_warm(int device);
 // load the kernels the initialisation launches (cudaFuncGetAttributes on each)
 cudaError_t preload_radix_kernels();
 cudaError_t preload_reorder_kernels();
-cudaError_t preload_ttmc_init_kernels();
 
 // ---- K-b: TTMc (ttmc.cu)
 tucker_status launch_ttmc(Ctx *c, int mode, float *Y, cudaStream_t s);

@@ -904,11 +904,6 @@ __global__ void fill_iota_ones_kernel(uint32_t *iota, float *ones, int64_t n) {
   }
 }
 
-cudaError_t preload_ttmc_init_kernels() {
-  cudaFuncAttributes fa;
-  return cudaFuncGetAttributes(&fa, fill_iota_ones_kernel);
-}
-
 void fill_iota_ones(uint32_t *iota, float *ones, int64_t n, cudaStream_t s) {
   const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 65535));
   fill_iota_ones_kernel<<<blocks, 256, 0, s>>>(iota, ones, n);
