@@ -519,7 +519,10 @@ def run_mine(args):
                        "precision": "TTMc FP32 (FP32 products and sums); QRP: FP64 storage, norms, reflectors, R "
                                     "and T, with A^T y summed in double-float FP32 pairs around a power-of-two "
                                     "offset (about 2^-49 s1 per product) and Q formed as double-float sums; core "
-                                    "and fit FP64", "replicas": world},
+                                    "on the tensor cores: Y (FP32) and U_N (FP64) cut into four exact 8-bit "
+                                    "fixed-point slices per column, BF16 products summed exactly (integer) in "
+                                    "FP32 tensor memory, levels combined in 64-bit integers, row ranges and fit "
+                                    "in FP64", "replicas": world},
             "hooi_s_per_iter": ms_per_step * 1e-3,
             "step": "one HOOI sweep (TTMc + QRP per mode, core, fit) replayed from a CUDA graph of the whole iteration",
             "eager_ms_per_step": eager_ms,

@@ -1,11 +1,14 @@
-"""The opt-in core tensor on the tensor cores (TUCKER_CORE_TC=1: tcgen05 kind::f16, every
-FP32 input split exactly into three BF16 pieces, six products, FP32 accumulation in tensor
-memory over 16 rows, then FP64; Section III-B, eq. core_unfolded: G_(N) = U_N^T Y_(N))
-against the FP64 oracle's core of the same Y_(N) and U_N (the GPU's own TTMc output and
-FP32 factor copy), and against the default FP64 SIMT form of the same sweep.
+"""The core tensor on the tensor cores (core_tc_kernel: tcgen05 kind::f16; Section III-B,
+eq. core_unfolded: G_(N) = U_N^T Y_(N)) against the FP64 oracle's core of the same Y_(N) and
+U_N (the GPU's own TTMc output and FP64 factor), and against the FP64 SIMT form of the same
+sweep (TUCKER_CORE_TC=0).
 
-Bar: relative Frobenius error 2e-6 on G (FP32-class: the dropped products are about 2^-23
-of a product and the tensor-memory accumulation rounds in FP32), fits within 1e-7."""
+The tensor-core form splits Y's columns and U's columns into four 8-bit fixed-point slices
+against a shared power of two per column and row range; every tensor-memory accumulation is
+an exact integer sum.  Its only errors are the parts of Y and U below the last slice
+(under 2^-33 of the column's largest entry; for an entry of G at most sqrt(I_N) 2^-32 of the
+largest entry of its Y column) and FP64 additions.  Bars: relative Frobenius error 1e-8 on G,
+fits within 1e-8 of the FP64 form."""
 import os
 
 import numpy as np
@@ -13,7 +16,7 @@ import pytest
 
 import oracle
 from paper_2010_10638_gb300 import synth
-from tests.gpu_util import f32_round, lib, rel_fro, torch
+from tests.gpu_util import lib, rel_fro, torch
 
 pytestmark = pytest.mark.gpu
 
@@ -43,13 +46,13 @@ def test_tensor_core_core_matches_oracle(dims, ranks, nnz, monkeypatch):
         # the same step from the same Y_(N) and U_N: the FP64 oracle and the FP64 SIMT form
         Y = T.ttmc_mode(ctx, N - 1).cpu().numpy().astype(np.float64)
         U = T.tucker_get_factor(ctx, N - 1).cpu().numpy()
-        G_ref = oracle.core(Y, f32_round([U])[0], ranks)
+        G_ref = oracle.core(Y, U, ranks)
         err = rel_fro(G_tc, G_ref)
-        assert err <= 2e-6, f"core: relative error {err:.2e}"
+        assert err <= 1e-8, f"core: relative error {err:.2e}"
     finally:
         T.tucker_free(ctx)
-    # the default FP64 SIMT form of the whole sweep: same fit to the accuracy of the core
-    monkeypatch.delenv("TUCKER_CORE_TC", raising=False)
+    # the FP64 SIMT form of the whole sweep: same fit to the accuracy of the core
+    monkeypatch.setenv("TUCKER_CORE_TC", "0")
     ctx = T.tucker_init(dims, torch.as_tensor(w.coords.astype(np.int32)).cuda(), torch.as_tensor(w.vals).cuda(),
                         ranks, [torch.as_tensor(u).cuda() for u in w.U0], direct=True)
     try:
@@ -57,5 +60,5 @@ def test_tensor_core_core_matches_oracle(dims, ranks, nnz, monkeypatch):
         G64 = T.core_tensor(ctx).cpu().numpy()
     finally:
         T.tucker_free(ctx)
-    assert rel_fro(G_tc, G64) <= 2e-6
-    assert abs(fit_tc - fit64) <= 1e-7
+    assert rel_fro(G_tc, G64) <= 1e-8
+    assert abs(fit_tc - fit64) <= 1e-8
