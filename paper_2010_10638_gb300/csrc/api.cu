@@ -173,6 +173,14 @@ static tucker_status init_impl(Ctx *c, const uint32_t *coords, const float *vals
     }
   }
   TK_CUDA(dev_alloc(c, &c->gram, (size_t)gram_max));
+  {
+    size_t gp = 0;
+    for (int n = 0; n < N; ++n) {
+      const ModeCopy &mc = c->mode[n];
+      if (qrp_n_cols(c, n) == mc.I && mc.P > mc.I) gp = std::max(gp, gram_part_elems(mc.I));
+    }
+    if (gp) TK_CUDA(dev_alloc(c, &c->gram_part, gp));
+  }
   TK_CUDA(dev_alloc(c, &c->G, (size_t)PR));
   TK_CUDA(dev_alloc(c, &c->core_part, core_part_elems(c->num_sms, c->mode[N - 1].P, c->ranks[N - 1])));
   TK_CUDA(dev_alloc(c, &c->core_counter, 4));
@@ -256,7 +264,7 @@ static tucker_status hooi_impl(Ctx *c, double *fit_out, cudaStream_t s) {
     qrp_bind_work(&w, c->qw.V, mc.I, ncols, k, c->num_sms);
     w.err_out = c->d_err;  // a timed-out wait is reported by the next synchronising call
     if (ncols == mc.I && mc.P > mc.I) {
-      gram_f32(c->Y, mc.I, mc.P, c->gram, s);
+      launch_gram(c, c->Y, mc.I, mc.P, c->gram, s);
       st = qrp_run_f64(c->gram, mc.I, mc.I, mc.I, k, c->U64[n], k, nullptr, nullptr, &w, c->num_sms, s);
     } else {
       st = qrp_run_f32(c->Y, mc.I, mc.P, mc.P, k, c->U64[n], k, nullptr, nullptr, &w, c->num_sms, s);

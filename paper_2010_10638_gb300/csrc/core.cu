@@ -428,6 +428,249 @@ __global__ void __launch_bounds__(kRedT) core_reduce_kernel(const double *part, 
   }
 }
 
+static bool core_on_tensor_cores();
+
+// ---------------------------------------------------------------- Gram matrix on the tensor cores
+// S = Y Y^T (m x m) of an FP32 m x n matrix, for the fat unfoldings of Section III-D, with
+// the exact fixed-point slices of the core: one CTA computes a 128 x 64 tile of S (rows i
+// of Y as the MMA's M, rows j as its N) over a range of columns c (the K), 128 columns at
+// a time.  For each 128-column block every row of Y gets a shared power of two over the
+// block, the slices' level sums are exact integers in tensor memory (products <= 2^16, at
+// most 128 columns), and after each block they are combined in 64-bit integers and added,
+// scaled, into FP64 registers.  The column ranges are added in a fixed order afterwards.
+constexpr int kGmM = 128;           // rows i per tile (MMA M)
+constexpr int kGmN = 64;            // rows j per tile (MMA N)
+constexpr int kGmCols = 128;        // columns per exact block
+constexpr int kGmLd = kGmCols + 1;  // shared-memory row stride of the staged block (no bank conflicts)
+constexpr int kGramMaxRows = 1024;  // larger Gram matrices use the FP64 form
+constexpr int kGramMaxRanges = 8;   // column ranges (partial sets)
+
+__host__ __device__ constexpr size_t gm_smem_bytes() {
+  return (size_t)(kGmM + kGmN) * kGmLd * 4                                // the rows' column block
+         + (size_t)2 * kTcSlices * (kGmM + kGmN) * kTcK * 2 + 128;        // two slice buffers
+}
+
+__global__ void __launch_bounds__(128) gram_tc_kernel(const float *Y, int64_t m, int64_t n, int64_t cols_per_range,
+                                                      double *part, uint32_t *err) {
+  constexpr uint32_t kCols = tc_tmem_cols(kGmN);
+  constexpr int kASlice = kGmM * kTcK, kBSlice = kGmN * kTcK;
+  extern __shared__ unsigned char gm_raw[];
+  unsigned char *base = reinterpret_cast<unsigned char *>(
+      (reinterpret_cast<uintptr_t>(gm_raw) + 127) & ~static_cast<uintptr_t>(127));
+  float *sYa = reinterpret_cast<float *>(base);  // [kGmM][kGmLd]: rows i of the block
+  float *sYb = sYa + kGmM * kGmLd;               // [kGmN][kGmLd]: rows j
+  __nv_bfloat16 *sA = reinterpret_cast<__nv_bfloat16 *>(
+      base + ((size_t)(kGmM + kGmN) * kGmLd * 4 + 127) / 128 * 128);
+  __nv_bfloat16 *sB = sA + 2 * kTcSlices * kASlice;
+  __shared__ __align__(8) unsigned long long bar[2];
+  __shared__ uint32_t tbase;
+  __shared__ int s_ok;
+  __shared__ int s_eb[kGmN];
+  __shared__ float s_bsc[2][kGmN];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int64_t i0 = (int64_t)blockIdx.x * kGmM, j0 = (int64_t)blockIdx.y * kGmN;
+  const int64_t c_begin = (int64_t)blockIdx.z * cols_per_range;
+  const int64_t c_end = min(n, c_begin + cols_per_range);
+  uint32_t sb[2];
+  sb[0] = (uint32_t)__cvta_generic_to_shared(&bar[0]);
+  sb[1] = (uint32_t)__cvta_generic_to_shared(&bar[1]);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sb[0]) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sb[1]) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_ok = 1;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(&tbase)),
+                 "r"(kCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tbase;
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kGmN >> 3) << 17) | ((uint32_t)(kGmM >> 4) << 24);
+  const uint32_t lbo = 128, sbo = kTcKC * 128;
+  const uint32_t aS = (uint32_t)__cvta_generic_to_shared(sA), bS = (uint32_t)__cvta_generic_to_shared(sB);
+  const int64_t ri = i0 + tid;  // this thread's row i (TMEM lane)
+  double accd[kGmN];
+#pragma unroll
+  for (int q = 0; q < kGmN; ++q) accd[q] = 0.0;
+  bool ok = true;
+  int phase[2] = {0, 0};  // completions waited for, per buffer
+  int issued[2] = {0, 0};  // products issued, per buffer
+  int jglob = 0;           // chunk counter over all blocks (buffer = jglob & 1)
+  for (int64_t cb = c_begin; cb < c_end && ok; cb += kGmCols) {
+    const int ncb = (int)min((int64_t)kGmCols, c_end - cb);
+    const int nch = (ncb + kTcK - 1) / kTcK;
+    // the block's columns of rows i and rows j, zero-padded (coalesced along the rows)
+#pragma unroll 8
+    for (int q = tid; q < kGmM * kGmCols; q += 128) {
+      const int r = q / kGmCols, k = q % kGmCols;
+      const int64_t rr = i0 + r;
+      sYa[r * kGmLd + k] = (rr < m && k < ncb) ? __ldg(Y + rr * n + cb + k) : 0.f;
+    }
+#pragma unroll 8
+    for (int q = tid; q < kGmN * kGmCols; q += 128) {
+      const int r = q / kGmCols, k = q % kGmCols;
+      const int64_t rj = j0 + r;
+      sYb[r * kGmLd + k] = (rj < m && k < ncb) ? __ldg(Y + rj * n + cb + k) : 0.f;
+    }
+    __syncthreads();
+    uint32_t abits = 0;
+    for (int k = 0; k < ncb; ++k) abits = max(abits, __float_as_uint(sYa[tid * kGmLd + k]) & 0x7fffffffu);
+    const int ea = above_exp_f32(abits);
+    const int ash = 8 - ea, ash1 = min(ash, 120);
+    const float asc1 = __int_as_float((127 + ash1) << 23), asc2 = __int_as_float((127 + ash - ash1) << 23);
+    if (tid < kGmN) {
+      uint32_t bbits = 0;
+      for (int k = 0; k < ncb; ++k) bbits = max(bbits, __float_as_uint(sYb[tid * kGmLd + k]) & 0x7fffffffu);
+      const int eb = above_exp_f32(bbits), bsh = 8 - eb, bsh1 = min(bsh, 120);
+      s_eb[tid] = eb;
+      s_bsc[0][tid] = __int_as_float((127 + bsh1) << 23);
+      s_bsc[1][tid] = __int_as_float((127 + bsh - bsh1) << 23);
+    }
+    __syncthreads();
+    for (int j = 0; j < nch && ok; ++j, ++jglob) {
+      const int b = jglob & 1;
+      if (issued[b] > phase[b]) {  // the products that last read this buffer
+        ok = tc_wait(sb[b], (uint32_t)(phase[b] & 1));
+        ++phase[b];
+      }
+      ok = __syncthreads_and(ok ? 1 : 0) != 0;
+      if (!ok) break;
+      __nv_bfloat16 *a = sA + (size_t)b * kTcSlices * kASlice;
+      __nv_bfloat16 *bb = sB + (size_t)b * kTcSlices * kBSlice;
+#pragma unroll 4
+      for (int k = 0; k < kTcK; ++k) slices_f32(sYa[tid * kGmLd + j * kTcK + k], asc1, asc2, a + kmaj16(tid, k), kASlice);
+      for (int q = tid; q < kGmN * kTcK; q += 128) {
+        const int r = q / kTcK, k = q % kTcK;
+        slices_f32(sYb[r * kGmLd + j * kTcK + k], s_bsc[0][r], s_bsc[1][r], bb + kmaj16(r, k), kBSlice);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (tid == 0) {
+        const uint32_t aB = aS + (uint32_t)(b * kTcSlices * kASlice * 2), bB = bS + (uint32_t)(b * kTcSlices * kBSlice * 2);
+#pragma unroll
+        for (int L = 0; L < kTcLevels; ++L) {
+          const int s0 = L < kTcSlices ? 0 : L - (kTcSlices - 1);
+          const int s1 = L < kTcSlices ? L : kTcSlices - 1;
+          for (int sa = s0; sa <= s1; ++sa) {
+            const uint64_t ad = umma_desc(aB + (uint32_t)(sa * kASlice * 2), lbo, sbo);
+            const uint64_t bd = umma_desc(bB + (uint32_t)((L - sa) * kBSlice * 2), lbo, sbo);
+            const uint32_t acc = (j > 0 || sa != s0) ? 1u : 0u;  // a fresh accumulation per block
+            asm volatile(
+                "{ .reg .pred p; setp.ne.u32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(
+                    tmem + (uint32_t)(L * kGmN)),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                : "memory");
+          }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(sb[b])
+                     : "memory");
+      }
+      ++issued[b];
+    }
+    // this block's products complete (both buffers), then its levels into FP64
+    for (int b = 0; b < 2 && ok; ++b)
+      while (issued[b] > phase[b] && ok) {
+        ok = tc_wait(sb[b], (uint32_t)(phase[b] & 1));
+        ++phase[b];
+      }
+    ok = __syncthreads_and(ok ? 1 : 0) != 0;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!ok) break;
+#pragma unroll
+    for (int n0 = 0; n0 < kGmN; n0 += 16) {  // 16 columns of j at a time: five levels, then FP64
+      long long accx[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) accx[q] = 0;
+#pragma unroll
+      for (int L = 0; L < kTcLevels; ++L) {
+        uint32_t v[16];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(L * kGmN + n0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+          accx[q] += (long long)__float2int_rn(__uint_as_float(v[q])) << (8 * (kTcLevels - 1 - L));
+      }
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int sh = ea + s_eb[n0 + q] - 16 - 8 * (kTcLevels - 1);
+        const int sh1 = min(max(sh, -1000), 1000);
+        accd[n0 + q] += ((double)accx[q] * pow2d(sh1)) * pow2d(sh - sh1);
+      }
+    }
+    // every warp has read the levels (and s_eb) before the next block overwrites them
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  }
+  if (!ok && tid == 0) {  // give products still in flight (bounded) time to end, then record
+    for (int b = 0; b < 2; ++b)
+      while (issued[b] > phase[b]) {
+        tc_wait(sb[b], (uint32_t)(phase[b] & 1));
+        ++phase[b];
+      }
+    atomicOr(err, kErrTimeout);
+    s_ok = 0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (ri < m)
+#pragma unroll
+    for (int q = 0; q < kGmN; ++q)
+      if (j0 + q < m)
+        part[(int64_t)blockIdx.z * m * m + ri * m + j0 + q] = s_ok ? accd[q] : __longlong_as_double(0x7ff8000000000000ll);
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
+}
+
+// S[q] = the column ranges' partials added in order
+__global__ void gram_reduce_kernel(const double *part, int nr, int64_t mm, double *S) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < mm; q += (int64_t)gridDim.x * blockDim.x) {
+    double t = 0.0;
+    for (int r = 0; r < nr; ++r) t += __ldcg(part + (int64_t)r * mm + q);
+    S[q] = t;
+  }
+}
+
+size_t gram_part_elems(int64_t m) {
+  return (m > 0 && m <= kGramMaxRows) ? (size_t)kGramMaxRanges * (size_t)(m * m) : 0;
+}
+
+void launch_gram(Ctx *c, const float *Y, int64_t m, int64_t n, double *S, cudaStream_t s) {
+  if (!core_on_tensor_cores() || !c->gram_part || m > kGramMaxRows || m < 1 || n < 1) {
+    gram_f32(Y, m, n, S, s);
+    return;
+  }
+  const int64_t ti = (m + kGmM - 1) / kGmM, tj = (m + kGmN - 1) / kGmN;
+  // column ranges: enough CTAs to reach about 2 x SMs, at most kGramMaxRanges, at least 32 columns each
+  int64_t nr = std::max<int64_t>(1, std::min<int64_t>((2 * (int64_t)c->num_sms) / (ti * tj), kGramMaxRanges));
+  nr = std::min<int64_t>(nr, std::max<int64_t>(1, n / 32));
+  const int64_t cpr = (n + nr - 1) / nr;
+  nr = (n + cpr - 1) / cpr;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cap);
+  if (cap == cudaStreamCaptureStatusNone)
+    cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gm_smem_bytes());
+  gram_tc_kernel<<<dim3((unsigned)ti, (unsigned)tj, (unsigned)nr), 128, gm_smem_bytes(), s>>>(Y, m, n, cpr,
+                                                                                           c->gram_part, c->d_err);
+  ::tk::count_launch();
+  const int64_t mm = m * m;
+  gram_reduce_kernel<<<(unsigned)std::min<int64_t>((mm + 255) / 256, 4096), 256, 0, s>>>(c->gram_part, (int)nr, mm, S);
+  ::tk::count_launch();
+}
+
 // The core runs on the tensor cores (core_tc_kernel + core_reduce_kernel) where R <= 64 and
 // the row ranges fit the partial buffer; TUCKER_CORE_TC=0 selects the FP64 SIMT form
 // (core_kernel) instead.  Both agree to FP64 rounding: on the 1M-nonzero Zipf workload

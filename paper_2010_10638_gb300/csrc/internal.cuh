@@ -117,6 +117,7 @@ struct Ctx {
   uint32_t *fib_iota = nullptr;  // fiber form: 0, 1, ..., F-1 (max F)
   float *fib_ones = nullptr;   // fiber form: 1.0f (max F)
   double *gram = nullptr;      // Y Y^T for fat unfoldings
+  double *gram_part = nullptr; // column-range partials of the tensor-core Gram matrix
   double *G = nullptr;         // core tensor of the last sweep
   double *fit_dev = nullptr;   // fit of the last sweep (device)
   double *norm_dev = nullptr;  // [0] ||X||^2, [1] ||G||^2
@@ -226,6 +227,9 @@ tucker_status qrp_run_f64(const double *A, int64_t m, int64_t n, int64_t lda, in
 tucker_status qrp_run_f32(const float *A, int64_t m, int64_t n, int64_t lda, int k, double *Q, int64_t ldq,
                           int64_t *piv, double *rdiag, QrpWork *w, int nb, cudaStream_t s);
 void gram_f32(const float *Y, int64_t m, int64_t n, double *S, cudaStream_t s);
+// S = Y Y^T on the tensor cores where it fits (m <= 1024, c->gram_part allocated), else gram_f32
+void launch_gram(Ctx *c, const float *Y, int64_t m, int64_t n, double *S, cudaStream_t s);
+size_t gram_part_elems(int64_t m);  // partial buffer of launch_gram for an m x m Gram matrix (0: none)
 int qrp_blocks(int num_sms, int64_t m);
 tucker_status launch_wait_selftest(Ctx *c, unsigned long long max_polls, cudaStream_t s);
 
