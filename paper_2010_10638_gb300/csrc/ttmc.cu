@@ -410,150 +410,52 @@ __global__ void __launch_bounds__(kTtmcWarps * 32) ttmc_pipe_kernel(const TtmcPa
 //      (an identity index into t), so slices, split slices and the fixup are shared.
 //
 // Pass 1: one warp per run of `fpw` fibers (any run of whole fibers will do: t_f does not
-// depend on slices), windows of 32 consecutive nonzeros.  Lane (p, q) owns the
-// column quad q (t_f[4q, 4q+4)) of the QL = RB/4 consecutive positions of block p; the QL
-// lanes of a block read one whole factor row per position (coalesced), values and indices
-// come by shuffle from the coalesced loads (lane = position).  Each lane adds its positions
-// in order, writing the fibers that start and end inside its block; the piece before its
-// first fiber start (lead) and after its last (trail) are joined across blocks by a shuffle
-// scan over the maps "A -> A + lead" (no start) and "A -> trail" (a start), in block order,
-// applied to the fiber left open by the previous window.  Fixed orders: t is reproducible.
+// depend on slices).  One fiber per group of QL = RB/4 lanes (lane q of the group owns the
+// column quad t_f[4q, 4q+4)), 32/QL fibers of the warp side by side; a group adds its
+// fiber's positions in order (fibers are at most kFiberCap long), with the values, indices
+// and factor rows of four positions in flight at a time.  One fixed order: t is reproducible.
 template <int RB>
 __global__ void __launch_bounds__(kTtmcWarps * 32) ttmc_fibsum_kernel(const TtmcParams p, float *__restrict__ T,
                                                                      int64_t fpw) {
-  constexpr int QL = RB / 4;    // lanes (column quads) per position block
-  constexpr int PG = 32 / QL;   // position blocks per window
-  constexpr int PB = 32 / PG;   // positions per block (= QL)
+  constexpr int QL = RB / 4;   // lanes per fiber
+  constexpr int FG = 32 / QL;  // fibers side by side in a warp
   static_assert(RB % 4 == 0 && 32 % QL == 0, "RB in {4, 8, 16, 32}");
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t u = (int64_t)blockIdx.x * kTtmcWarps + w;  // this warp's fibers: [u fpw, u fpw + fpw)
   if (u * fpw >= (int64_t)p.Z) return;
-  const float *UB = static_cast<const float *>(p.U[1]);
+  const float4 *UB4 = static_cast<const float4 *>(p.U[1]);
   const uint32_t *idxB = p.idx[1];
-  const uint32_t f0 = (uint32_t)(u * fpw);
+  const int g = lane / QL, q = lane % QL;
+  const uint32_t f_begin = (uint32_t)(u * fpw);
   const uint32_t f_end = (uint32_t)min((int64_t)p.Z, u * fpw + fpw);
-  const uint32_t z0 = __ldg(p.fptr + f0), z1 = __ldg(p.fptr + f_end);
-  const int q = lane % QL, pb = lane / QL, P0 = pb * PB;
   float4 *T4 = reinterpret_cast<float4 *>(T);
-  uint32_t kb = f0;                           // fiber of the window's first nonzero
-  float4 carry = make_float4(0.f, 0.f, 0.f, 0.f);  // what fiber kb gathered in earlier windows
-  float x = 0.f;
-  uint32_t ib = 0u;
-  if (z0 + lane < z1) {
-    x = __ldg(p.val + z0 + lane);
-    ib = __ldg(idxB + z0 + lane);
-  }
-  uint32_t bound = (kb + 1u + lane <= p.Z) ? __ldg(p.fptr + kb + 1u + lane) : 0xffffffffu;
-  for (uint32_t z = z0; z < z1; z += 32u) {
-    const int nt = (int)min(32u, z1 - z);
-    const uint32_t qq = bound - z;
-    uint32_t starts = __reduce_or_sync(kFull, qq < 32u ? (1u << qq) : 0u);  // bit s: a fiber starts at s (s >= 1)
-    starts &= (nt >= 32) ? kFull : ((1u << nt) - 1u);
-    const bool end_is_start = __any_sync(kFull, qq == (uint32_t)nt);
-    const uint32_t kb_next = kb + __popc(__ballot_sync(kFull, qq <= (uint32_t)nt));
-    const uint32_t bound_next = (kb_next + 1u + lane <= p.Z) ? __ldg(p.fptr + kb_next + 1u + lane) : 0xffffffffu;
-    float xn = 0.f;
-    uint32_t ibn = 0u;
-    if (z + 32u + lane < z1) {
-      xn = __ldg(p.val + z + 32u + lane);
-      ibn = __ldg(idxB + z + 32u + lane);
-    }
-    auto fiber_of = [&](int s) { return kb + (uint32_t)__popc(starts & ((2u << s) - 1u)); };
-    // this block's rows: all loads first
-    float xv[PB];
-    float4 r[PB];
+  for (uint32_t fr = f_begin; fr < f_end; fr += FG) {
+    const uint32_t f = fr + (uint32_t)g;
+    if (f >= f_end) continue;
+    const uint32_t zs = __ldg(p.fptr + f), ze = __ldg(p.fptr + f + 1);
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (uint32_t z = zs; z < ze; z += 4u) {
+      float xv[4];
+      uint32_t iv[4];
 #pragma unroll
-    for (int i = 0; i < PB; ++i) {
-      xv[i] = __shfl_sync(kFull, x, P0 + i);
-      const uint32_t rr = __shfl_sync(kFull, ib, P0 + i);
-      r[i] = (P0 + i < nt) ? __ldg(reinterpret_cast<const float4 *>(UB + (size_t)rr * RB) + q)
-                           : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    // local pass: lead piece, fibers inside the block, trail piece
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f), lead = acc;
-    bool seen = false;
-#pragma unroll
-    for (int i = 0; i < PB; ++i) {
-      if ((starts >> (P0 + i)) & 1u) {  // the fiber at P0 + i - 1 ends
-        if (seen)
-          T4[(size_t)fiber_of(P0 + i - 1) * QL + q] = acc;
-        else
-          lead = acc;
-        seen = true;
-        acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int k = 0; k < 4; ++k) {
+        const bool in = z + (uint32_t)k < ze;
+        xv[k] = in ? __ldg(p.val + z + k) : 0.f;
+        iv[k] = in ? __ldg(idxB + z + k) : 0u;
       }
-      acc.x = fmaf(xv[i], r[i].x, acc.x);
-      acc.y = fmaf(xv[i], r[i].y, acc.y);
-      acc.z = fmaf(xv[i], r[i].z, acc.z);
-      acc.w = fmaf(xv[i], r[i].w, acc.w);
-    }
-    if (!seen) lead = acc;
-    // block map: A -> (seen ? 0 : A) + (seen ? trail : lead); inclusive scan over blocks
-    bool cz = seen;  // composed map resets A
-    float4 cb = seen ? acc : lead;
+      float4 r[4];
 #pragma unroll
-    for (int d = 1; d < PG; d <<= 1) {
-      const bool ez = __shfl_up_sync(kFull, (int)cz, d * QL) != 0;
-      float4 eb;
-      eb.x = __shfl_up_sync(kFull, cb.x, d * QL);
-      eb.y = __shfl_up_sync(kFull, cb.y, d * QL);
-      eb.z = __shfl_up_sync(kFull, cb.z, d * QL);
-      eb.w = __shfl_up_sync(kFull, cb.w, d * QL);
-      if (pb >= d && !cz) {  // (this, covering later blocks) after (earlier): keep earlier's reset, add
-        cz = ez;
-        cb.x = eb.x + cb.x;
-        cb.y = eb.y + cb.y;
-        cb.z = eb.z + cb.z;
-        cb.w = eb.w + cb.w;
+      for (int k = 0; k < 4; ++k)
+        r[k] = (z + (uint32_t)k < ze) ? __ldg(UB4 + (size_t)iv[k] * QL + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        acc.x = fmaf(xv[k], r[k].x, acc.x);
+        acc.y = fmaf(xv[k], r[k].y, acc.y);
+        acc.z = fmaf(xv[k], r[k].z, acc.z);
+        acc.w = fmaf(xv[k], r[k].w, acc.w);
       }
     }
-    // open fiber entering this block = (composition of blocks before it)(carry)
-    const bool pz = __shfl_up_sync(kFull, (int)cz, QL) != 0;
-    float4 pbv;
-    pbv.x = __shfl_up_sync(kFull, cb.x, QL);
-    pbv.y = __shfl_up_sync(kFull, cb.y, QL);
-    pbv.z = __shfl_up_sync(kFull, cb.z, QL);
-    pbv.w = __shfl_up_sync(kFull, cb.w, QL);
-    float4 open = carry;
-    if (pb > 0) {
-      if (pz) {
-        open = pbv;
-      } else {
-        open.x = carry.x + pbv.x;
-        open.y = carry.y + pbv.y;
-        open.z = carry.z + pbv.z;
-        open.w = carry.w + pbv.w;
-      }
-    }
-    if (seen) {  // the open fiber ends at this block's first start
-      const int s0 = __ffs(starts & (((PB + P0) >= 32 ? kFull : ((1u << (P0 + PB)) - 1u)) & ~((1u << P0) - 1u))) - 1;
-      T4[(size_t)fiber_of(s0 - 1) * QL + q] =
-          make_float4(open.x + lead.x, open.y + lead.y, open.z + lead.z, open.w + lead.w);
-    }
-    // the fiber open at the end of the window: the last block's composition applied to carry
-    const int last = PG - 1;
-    const bool lz = __shfl_sync(kFull, (int)cz, last * QL + q) != 0;
-    float4 fin;
-    fin.x = __shfl_sync(kFull, cb.x, last * QL + q);
-    fin.y = __shfl_sync(kFull, cb.y, last * QL + q);
-    fin.z = __shfl_sync(kFull, cb.z, last * QL + q);
-    fin.w = __shfl_sync(kFull, cb.w, last * QL + q);
-    if (!lz) {
-      fin.x = carry.x + fin.x;
-      fin.y = carry.y + fin.y;
-      fin.z = carry.z + fin.z;
-      fin.w = carry.w + fin.w;
-    }
-    if (end_is_start || z + (uint32_t)nt == z1) {
-      if (pb == 0) T4[(size_t)fiber_of(nt - 1) * QL + q] = fin;
-      carry = make_float4(0.f, 0.f, 0.f, 0.f);
-    } else {
-      carry = fin;
-    }
-    kb = kb_next;
-    bound = bound_next;
-    x = xn;
-    ib = ibn;
+    T4[(size_t)f * QL + q] = acc;
   }
 }
 
@@ -1559,12 +1461,13 @@ static cudaError_t run_pipe(const TtmcParams &p, cudaStream_t s) {
 
 template <int RB>
 static cudaError_t run_fibsum(const TtmcParams &p, float *T, int64_t nnz, cudaStream_t s) {
-  // 64 fibers per warp (measured best on the skewed 20M-nonzero workload; many short warps
-  // balance the Zipf-skewed fiber lengths)
+  // two rounds of side-by-side fibers per warp (16 fibers for RB = 16: measured best on the
+  // skewed 20M-nonzero workload against 8, 24, 32, 64, 128; short warps balance the
+  // Zipf-skewed fiber lengths)
   const int64_t F = std::max<int64_t>(p.Z, 1);
   (void)nnz;
-  int64_t fpw = 64;
-  if (const char *e = std::getenv("TUCKER_FIBSUM_FPW")) fpw = std::max<int64_t>(32, std::atoll(e) / 32 * 32);
+  int64_t fpw = 2 * (32 / (RB / 4));
+  if (const char *e = std::getenv("TUCKER_FIBSUM_FPW")) fpw = std::max<int64_t>(4, std::atoll(e) / 4 * 4);
   const int64_t warps = (F + fpw - 1) / fpw;
   const unsigned blocks = (unsigned)((warps + kTtmcWarps - 1) / kTtmcWarps);
   ttmc_fibsum_kernel<RB><<<blocks, kTtmcWarps * 32, 0, s>>>(p, T, fpw);

@@ -18,9 +18,9 @@ Two bars.
      nonzero form: the lanes of a group add every NG-th nonzero of a work unit in order
        (at most min(k_i, chunk) terms), 5 shuffle levels merge the groups, and a row split
        over p pieces adds them in the fixup kernel (ceil(p/8) + 8 additions);
-     fiber form: a fiber's sum t_f takes at most fiber_cap + 8 additions (block run, block
-       scan, window carry), the update adds at most min(k_i, fchunk) fiber terms per unit
-       plus 5 shuffle levels, and the fixup as above over the fiber pieces.
+     fiber form: a fiber's sum t_f adds its at most fiber_cap nonzeros in order, the update
+       adds at most min(k_i, fchunk) fiber terms per unit plus 5 shuffle levels, and the
+       fixup as above over the fiber pieces.
    This holds whatever the conditioning: after sweeps on a tensor of structureless random
    values (fit near 0) some sampled rows cancel almost exactly, and an error relative to
    |Y| itself has no fixed bar there.  The BF16-factor form adds one BF16 rounding
@@ -56,7 +56,7 @@ def summation_depth(info, k, bf16):
         return np.where(pieces > 1, np.ceil(pieces / 8.0) + 8, 0)
     if info["fibers_on"] and not bf16:
         fc = info["fchunk"]
-        return (info["fiber_cap"] + 8) + np.minimum(k, fc) + 5 + fixup(np.ceil(k / fc))
+        return info["fiber_cap"] + np.minimum(k, fc) + 5 + fixup(np.ceil(k / fc))
     c = info["chunk"]
     return np.minimum(k, c) + 5 + fixup(np.ceil(k / c))
 
