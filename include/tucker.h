@@ -279,6 +279,17 @@ TUCKER_API uint64_t tucker_kernel_launches(void);
  */
 TUCKER_API tucker_status tucker_selftest_wait(tucker_ctx *c, uint64_t max_polls, void *stream);
 
+/*
+ * Self-test of the initialisation sort's bounded look-back (no counterpart in the paper):
+ * one sort pass over two tiles of 8192 words is launched with a single block that claims
+ * the second tile, so the first tile's counts never appear; the block polls for them at
+ * most max_polls times, gives up, stores nothing and latches the timeout bit.  Uses its
+ * own small allocations on `stream` and synchronises it.
+ * Returns TUCKER_ETIMEOUT when the wait gave up as designed, TUCKER_OK if it did not,
+ * TUCKER_EINVAL for max_polls = 0 or above 2^22, TUCKER_ECUDA if a CUDA call failed.
+ */
+TUCKER_API tucker_status tucker_selftest_sort_wait(uint64_t max_polls, void *stream);
+
 TUCKER_API const char *tucker_status_str(tucker_status s);
 /* Text of the last error recorded on this context ("" if none); valid until the next call. */
 TUCKER_API const char *tucker_last_error(const tucker_ctx *c);

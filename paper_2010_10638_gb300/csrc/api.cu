@@ -418,6 +418,16 @@ int tucker_mode_info(const tucker_ctx *h, int mode, int64_t *out, int cap) {
   return n;
 }
 
+tucker_status tucker_selftest_sort_wait(uint64_t max_polls, void *stream) {
+  if (max_polls == 0 || max_polls > (1ull << 22)) return TUCKER_EINVAL;
+  uint32_t err = 0;
+  if (tk::radix_selftest_wait((uint32_t)max_polls, static_cast<cudaStream_t>(stream), &err) != 0) {
+    cudaGetLastError();
+    return TUCKER_ECUDA;
+  }
+  return (err & tk::kErrTimeout) ? TUCKER_ETIMEOUT : TUCKER_OK;
+}
+
 tucker_status tucker_selftest_wait(tucker_ctx *h, uint64_t max_polls, void *stream) {
   if (!h) return TUCKER_EINVAL;
   return tk::launch_wait_selftest(&h->c, (unsigned long long)max_polls, static_cast<cudaStream_t>(stream));

@@ -190,6 +190,8 @@ int radix_sort_records(int64_t n, const RadixRecords &r, const RadixKey *keys, i
                        int nvalid, const float *valid_vals, void *scratch, size_t scratch_bytes, uint32_t *err,
                        cudaStream_t s);
 void iota_u32(uint32_t *out, int64_t n, cudaStream_t s);
+// self-test of the bounded look-back: 0 and the error word in *err_out, or -2 (CUDA error)
+int radix_selftest_wait(uint32_t polls, cudaStream_t s, uint32_t *err_out);
 
 // ---- K-a: reorder (reorder.cu)
 tucker_status build_sorted_copies(Ctx *c, const uint32_t *coords, const float *vals, cudaStream_t s);

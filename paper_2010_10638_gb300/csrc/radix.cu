@@ -137,6 +137,7 @@ struct RxPassArgs {
   unsigned long long *status;          // [tiles][256], zeroed
   uint32_t *tile_ctr;                  // zeroed
   uint32_t *err;
+  uint32_t spin;                       // polls of one status word at most
 };
 
 __device__ __forceinline__ unsigned long long rx_load(const unsigned long long *p) {
@@ -251,7 +252,7 @@ __global__ void __launch_bounds__(kRxThreads, 2) rx_pass_kernel(RxPassArgs a) {
       unsigned long long v = rx_load(a.status + t * kRxBins + tid);
       uint32_t polls = 0;
       while ((v >> 32) == 0ull) {
-        if (++polls >= kRxSpin) break;
+        if (++polls >= a.spin) break;
         if (polls > 64) __nanosleep(128);
         v = rx_load(a.status + t * kRxBins + tid);
       }
@@ -470,6 +471,7 @@ int radix_sort_records(int64_t n, const RadixRecords &r, const RadixKey *keys, i
     a.status = status + (int64_t)k * tiles * kRxBins;
     a.tile_ctr = ctr + k;
     a.err = err;
+    a.spin = kRxSpin;
     if (n > 0) {
       rx_pass_kernel<<<(unsigned)tiles, kRxThreads, sizeof(RxSmem), s>>>(a);
       ::tk::count_launch();
@@ -482,6 +484,52 @@ int radix_sort_records(int64_t n, const RadixRecords &r, const RadixKey *keys, i
 __global__ void rx_iota_kernel(uint32_t *out, int64_t n) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
     out[e] = (uint32_t)e;
+}
+
+// One pass over two tiles run by a single block that claims the second tile (the tile
+// counter starts at 1): its look-back waits for counts that never come, gives up after
+// `polls` polls and stores nothing.  Returns the error word (kErrTimeout expected).
+int radix_selftest_wait(uint32_t polls, cudaStream_t s, uint32_t *err_out) {
+  const int64_t n = 2 * (int64_t)kRxTile;
+  uint32_t *words = nullptr;  // in [n], out [n], hist [256], counter, error word
+  unsigned long long *status = nullptr;
+  if (cudaMallocAsync(reinterpret_cast<void **>(&words), sizeof(uint32_t) * (size_t)(2 * n + kRxBins + 2), s) !=
+      cudaSuccess)
+    return -2;
+  if (cudaMallocAsync(reinterpret_cast<void **>(&status), sizeof(unsigned long long) * 2 * kRxBins, s) != cudaSuccess) {
+    cudaFreeAsync(words, s);
+    return -2;
+  }
+  uint32_t *in = words, *out = words + n, *hist = words + 2 * n, *ctr = hist + kRxBins, *err = ctr + 1;
+  const uint32_t one = 1u;
+  cudaError_t e = cudaMemsetAsync(words, 0, sizeof(uint32_t) * (size_t)(2 * n + kRxBins + 2), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(unsigned long long) * 2 * kRxBins, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ctr, &one, sizeof(uint32_t), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(rx_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(RxSmem));
+  if (e == cudaSuccess) {
+    RxPassArgs a{};
+    a.n = n;
+    a.nwords = 1;
+    a.key_word = 0;
+    a.shift = 0;
+    a.bits = 8;
+    a.in[0] = in;
+    a.out[0] = out;
+    a.hist = hist;
+    a.status = status;
+    a.tile_ctr = ctr;
+    a.err = err;
+    a.spin = polls;
+    rx_pass_kernel<<<1, kRxThreads, sizeof(RxSmem), s>>>(a);
+    e = cudaGetLastError();
+  }
+  *err_out = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(err_out, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(status, s);
+  cudaFreeAsync(words, s);
+  const cudaError_t e2 = cudaStreamSynchronize(s);
+  return (e == cudaSuccess && e2 == cudaSuccess) ? 0 : -2;
 }
 
 cudaError_t preload_radix_kernels() {

@@ -37,7 +37,8 @@ EXPORTS = ["tucker_init", "ttmc_mode", "qrp_leading", "qrp_leading_work_bytes", 
            "tucker_sync_status", "tucker_free", "tucker_status_str", "tucker_last_error", "tucker_set_profiling",
            "tucker_phase_times", "tucker_kernel_launches", "qrp_leading_noalloc", "qrp_leading_noalloc_max_bytes",
            "tucker_selftest_wait", "tucker_mode_info", "qrp_leading_sync_status",
-           "qrp_leading_noalloc_sync_status", "tucker_fp32_fma_tflops", "tucker_hooi_graph", "tucker_lib_setup"]
+           "qrp_leading_noalloc_sync_status", "tucker_fp32_fma_tflops", "tucker_hooi_graph", "tucker_lib_setup",
+           "tucker_selftest_sort_wait"]
 
 
 class TuckerError(RuntimeError):
@@ -102,6 +103,8 @@ def load(path: str = LIB_PATH):
     lib.tucker_fp32_fma_tflops.restype = dbl
     lib.tucker_mode_info.argtypes = [vp, cint, P(i64), cint]
     lib.tucker_mode_info.restype = cint
+    lib.tucker_selftest_sort_wait.argtypes = [u64, vp]
+    lib.tucker_selftest_sort_wait.restype = cint
     lib.tucker_lib_setup.argtypes = [cint]
     lib.tucker_lib_setup.restype = cint
     lib.tucker_kernel_launches.argtypes = []
@@ -411,3 +414,12 @@ def qrp_leading_noalloc(A: torch.Tensor, k: int, stream=None):
 
 def tucker_selftest_wait(ctx: Context, max_polls: int, stream=None) -> None:
     _check(load().tucker_selftest_wait(ctx.handle, int(max_polls), _stream(stream)), "tucker_selftest_wait", ctx)
+
+
+def tucker_selftest_sort_wait(max_polls: int, stream=None) -> str:
+    """Runs the sort's bounded look-back self-test; returns the status name
+    ("TUCKER_ETIMEOUT" when the wait gave up as designed)."""
+    rc = load().tucker_selftest_sort_wait(int(max_polls), _stream(stream))
+    if rc not in (0, 5):
+        _check(rc, "tucker_selftest_sort_wait")
+    return STATUS[rc]

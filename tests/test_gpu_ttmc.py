@@ -44,6 +44,7 @@ CASES = [
     ("order3-generic-r10", (200, 180, 160), (10, 10, 10), 25_013, "uniform"),
     ("order5-generic", (20, 18, 16, 14, 12), (3, 4, 2, 3, 2), 9_001, "uniform"),
     ("order3-long-slices", (5, 3000, 2000), (4, 16, 16), 50_000, "uniform"),
+    ("order8-generic", (9, 8, 7, 6, 5, 5, 4, 4), (2, 2, 2, 2, 2, 1, 2, 1), 12_007, "uniform"),
 ]
 
 
@@ -248,3 +249,16 @@ def test_lib_setup():
     w = synth.make("tiny-100^3")
     ctx = T.tucker_init(w.workload.dims, w.coords, w.vals, w.workload.ranks, w.U0)
     assert T.tucker_nnz(ctx) == w.workload.nnz
+
+
+def test_sort_lookback_wait_is_bounded():
+    """A sort pass whose look-back waits for counts that never come gives up after its
+    poll limit, reports TUCKER_ETIMEOUT, stores nothing, and the device stays usable."""
+    T = lib()
+    assert T.tucker_selftest_sort_wait(20_000) == "TUCKER_ETIMEOUT"
+    with pytest.raises(T.TuckerError):
+        T.tucker_selftest_sort_wait(0)
+    w = synth.make("tiny-100^3")
+    ctx = T.tucker_init(w.workload.dims, w.coords, w.vals, w.workload.ranks, w.U0)
+    assert T.tucker_nnz(ctx) == w.workload.nnz
+    assert 0.0 < T.hooi_iter(ctx) < 1.0
