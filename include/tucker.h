@@ -58,6 +58,10 @@ typedef enum {
 #define TUCKER_F_FIT_DEVICE 0x8u   /* hooi_iter writes the fit through a device pointer, no sync */
 #define TUCKER_F_UNPIPELINED 0x20u /* FP32 TTMc without the one-tile-ahead register prefetch
                                       (same arithmetic, kept for comparison) */
+#define TUCKER_F_TTMC_NORMS 0x40u /* hooi_iter: the QRP of Y_(n) takes its initial column norms
+                                     from the pipelined FP32 TTMc, which forms them as it writes
+                                     Y_(n) (ttmc_mode_norms), instead of its own first pass over
+                                     Y_(n); same results to rounding, not faster on GB300 */
 
 /*
  * tucker_lib_setup — optional one-time set-up of the library on a device: creates the
@@ -114,6 +118,19 @@ TUCKER_API tucker_status tucker_init(tucker_ctx **out, int order, const int64_t 
  * Deterministic: no atomics; the same inputs give bitwise the same Y.
  */
 TUCKER_API tucker_status ttmc_mode(tucker_ctx *c, int mode, float *Y, void *stream);
+
+/*
+ * ttmc_mode_norms — ttmc_mode, and the squared Euclidean norms of the columns of Y_(n)
+ * (the initial pivot norms of the QRP of Y_(n), Section III-D) formed as Y_(n) is written,
+ * without another pass over it; hooi_iter hands the same norms to its QRP.
+ *     colsq(c) = sum over i of Y_(n)(i, c)^2, exact FP32 squares summed in double-float
+ *                pairs within each block, then in a fixed order in FP64 (reproducible)
+ *   Y      device float [I_n x P_n], as for ttmc_mode (16-byte aligned)
+ *   colsq  device double [P_n], caller-owned, overwritten
+ * TUCKER_EINVAL where the mode's TTMc does not run the pipelined FP32 form that forms
+ * them (order 3, P_n <= 256, FP32 factors, not TUCKER_F_UNPIPELINED); Y is then written.
+ */
+TUCKER_API tucker_status ttmc_mode_norms(tucker_ctx *c, int mode, float *Y, double *colsq, void *stream);
 
 /*
  * qrp_leading — Householder QR with column pivoting truncated after k reflectors

@@ -181,6 +181,21 @@ static tucker_status init_impl(Ctx *c, const uint32_t *coords, const float *vals
     }
     if (gp) TK_CUDA(dev_alloc(c, &c->gram_part, gp));
   }
+  {  // column sums of squares from the pipelined TTMc: one row per block, one per split slice
+    int64_t rows = 0, pmax = 1;
+    for (int n = 0; n < N; ++n) {
+      const ModeCopy &mc = c->mode[n];
+      int64_t r = std::max(ttmc_pipe_blocks(mc.n_units) + mc.n_long, ttmc_pipe_blocks(mc.fn_units) + mc.fn_long);
+      r += (r + 63) / 64;  // the reduction's chunk sums (64 rows each)
+      rows = std::max(rows, r * mc.P);
+      pmax = std::max(pmax, mc.P);
+    }
+    TK_CUDA(dev_alloc(c, &c->sq_part, (size_t)std::max<int64_t>(rows, 1)));
+    TK_CUDA(dev_alloc(c, &c->colsq, (size_t)pmax));
+    TK_CUDA(dev_alloc(c, &c->sq_cnt, 8));
+    TK_CUDA(cudaMemsetAsync(c->sq_cnt, 0, 8 * sizeof(unsigned), s));
+    c->sq_elems = rows;
+  }
   TK_CUDA(dev_alloc(c, &c->G, (size_t)PR));
   TK_CUDA(dev_alloc(c, &c->core_part, core_part_elems(c->num_sms, c->mode[N - 1].P, c->ranks[N - 1])));
   TK_CUDA(dev_alloc(c, &c->core_counter, 4));
@@ -251,22 +266,28 @@ static tucker_status hooi_impl(Ctx *c, double *fit_out, cudaStream_t s) {
   if (st != TUCKER_OK) return st;
   for (int n = 0; n < N; ++n) {
     const ModeCopy &mc = c->mode[n];
+    const int ncols = qrp_n_cols(c, n);
+    const bool gram = ncols == mc.I && mc.P > mc.I;  // QRP of Y Y^T (fat Y_(n))
+    // with TUCKER_F_TTMC_NORMS the QRP of Y itself takes its initial column norms from the
+    // TTMc where that forms them
+    const bool want_norms = !gram && (c->flags & TUCKER_F_TTMC_NORMS);
+    bool norms = false;  // the TTMc left the column sums of squares of Y in c->colsq
     {
       Range r(kTtmcRange[n]);
-      st = launch_ttmc(c, n, c->Y, s);
+      st = want_norms ? launch_ttmc_norms(c, n, c->Y, c->colsq, &norms, s) : launch_ttmc(c, n, c->Y, s);
     }
     if (st == TUCKER_OK) st = mark(c, 2 * n + 1, s);
     if (st != TUCKER_OK) return st;
     Range rq(kQrpRange[n]);
     const int k = c->ranks[n];
-    const int ncols = qrp_n_cols(c, n);
     QrpWork w;
     qrp_bind_work(&w, c->qw.V, mc.I, ncols, k, c->num_sms);
     w.err_out = c->d_err;  // a timed-out wait is reported by the next synchronising call
-    if (ncols == mc.I && mc.P > mc.I) {
+    if (gram) {
       launch_gram(c, c->Y, mc.I, mc.P, c->gram, s);
       st = qrp_run_f64(c->gram, mc.I, mc.I, mc.I, k, c->U64[n], k, nullptr, nullptr, &w, c->num_sms, s);
     } else {
+      if (norms) w.colsq = c->colsq;
       st = qrp_run_f32(c->Y, mc.I, mc.P, mc.P, k, c->U64[n], k, nullptr, nullptr, &w, c->num_sms, s);
     }
     if (st != TUCKER_OK) return st;
@@ -500,6 +521,20 @@ tucker_status ttmc_mode(tucker_ctx *h, int mode, float *Y, void *stream) {
   if (reinterpret_cast<uintptr_t>(Y) % 16) return TUCKER_EINVAL;
   tk::Range r("ttmc_mode");
   return tk::launch_ttmc(&h->c, mode, Y, static_cast<cudaStream_t>(stream));
+}
+
+tucker_status ttmc_mode_norms(tucker_ctx *h, int mode, float *Y, double *colsq, void *stream) {
+  if (!h || !Y || !colsq || mode < 0 || mode >= h->c.N) return TUCKER_EINVAL;
+  if (reinterpret_cast<uintptr_t>(Y) % 16) return TUCKER_EINVAL;
+  tk::Range r("ttmc_mode_norms");
+  bool formed = false;
+  const tucker_status st = tk::launch_ttmc_norms(&h->c, mode, Y, colsq, &formed, static_cast<cudaStream_t>(stream));
+  if (st != TUCKER_OK) return st;
+  if (!formed) {
+    h->c.last_error = "column norms are formed by the pipelined FP32 TTMc only (order 3, P_n <= 256)";
+    return TUCKER_EINVAL;
+  }
+  return TUCKER_OK;
 }
 
 tucker_status hooi_iter(tucker_ctx *h, double *fit_out, void *stream) {

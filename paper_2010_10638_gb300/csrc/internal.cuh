@@ -85,6 +85,9 @@ struct QrpWork {
   int *nflag = nullptr;      // [64] per-step count of columns whose norm is recomputed
   unsigned *bar = nullptr;   // [4] grid barrier: arrivals, generation, error word, spare
   uint32_t *err_out = nullptr;  // where a timed-out barrier is reported (default &bar[2])
+  // [n] column sums of squares of A given by the caller (FP32 A), or nullptr: the cluster
+  // form then skips its own first pass over A and takes these as the initial norms
+  const double *colsq = nullptr;
   size_t bytes = 0;
 };
 
@@ -118,6 +121,11 @@ struct Ctx {
   float *fib_ones = nullptr;   // fiber form: 1.0f (max F)
   double *gram = nullptr;      // Y Y^T for fat unfoldings
   double *gram_part = nullptr; // column-range partials of the tensor-core Gram matrix
+  float2 *sq_part = nullptr;   // column sums of squares of Y_(n): [rows][P_n] double-float pairs,
+                               // one row per pipelined TTMc block, then one per split slice
+  int64_t sq_elems = 0;        // pairs in sq_part (with the reduction's chunk sums after the rows)
+  unsigned *sq_cnt = nullptr;  // [8] arrival counters of the norm reduction (zero between launches)
+  double *colsq = nullptr;     // [max P_n] column sums of squares of Y_(n), reduced from sq_part
   double *G = nullptr;         // core tensor of the last sweep
   double *fit_dev = nullptr;   // fit of the last sweep (device)
   double *norm_dev = nullptr;  // [0] ||X||^2, [1] ||G||^2
@@ -203,6 +211,10 @@ cudaError_t preload_reorder_kernels();
 
 // ---- K-b: TTMc (ttmc.cu)
 tucker_status launch_ttmc(Ctx *c, int mode, float *Y, cudaStream_t s);
+// launch_ttmc that also writes the column sums of squares of Y_(n) to colsq [P_n] where its
+// pipelined FP32 form runs (*formed true), at no extra pass over Y; *formed false otherwise.
+tucker_status launch_ttmc_norms(Ctx *c, int mode, float *Y, double *colsq, bool *formed, cudaStream_t s);
+int64_t ttmc_pipe_blocks(int64_t units);  // blocks of a pipelined TTMc launch over `units` units
 // TMA descriptors of the BF16 factor copies (host only; no device work)
 void make_factor_maps(Ctx *c);
 // 0, 1, ..., n-1 and n ones (the index and value streams of the fiber form's update pass)

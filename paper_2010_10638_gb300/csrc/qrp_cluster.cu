@@ -93,6 +93,8 @@ struct CArgs {
   int64_t ldq;
   int64_t *piv;
   double *rdiag;
+  const double *colsq;  // [n] column sums of squares of A given by the caller (FP32 A read as
+                        // float4 only), or nullptr: the first pass over A forms them
 };
 
 // Dynamic shared memory of one block; the same arithmetic on host and device.
@@ -670,6 +672,28 @@ __device__ void ccolsum(const CArgs &a, const AT *As, int64_t ncache, int64_t r0
 // swaps it into position j0.  When some block holds a norm flagged for exact
 // recomputation nothing is swapped and true is returned (the same answer in every
 // block).  The cluster barrier also publishes this step's F rows to the peers.
+// The norm bounds of the A^T y passes (layout of ccolsum's SQUARE pass) when the caller
+// gives the column sums of squares: each thread's pieces of its four columns are bounded by
+// the whole columns' norms.  Those are valid bounds, looser than the pieces' own norms by
+// about the square root of the number of pieces of a column, and so is each pass's offset.
+template <int NT>
+__device__ void nat_from_colsq(const CArgs &a, float *nat) {
+  const int64_t nq = a.n / 4;
+  const int cw = quad_cw(nq, NT);
+  const int nrl = NT / cw, cq = threadIdx.x % cw, rl = threadIdx.x / cw;
+  if (rl >= nrl) return;
+  float4 *nat4 = reinterpret_cast<float4 *>(nat);
+  constexpr float kMargin = 1.0f + 1.0f / 256.0f;  // covers the FP32 rounding of the bounds
+  for (int64_t q0 = 0, it = 0; q0 < nq; q0 += cw, ++it) {
+    const int64_t qc = q0 + cq;
+    if (qc >= nq) continue;  // no pass reads these
+    const double *cs = a.colsq + 4 * qc;
+    nat4[it * NT + threadIdx.x] =
+        make_float4(sqrtf((float)cs[0]) * kMargin, sqrtf((float)cs[1]) * kMargin, sqrtf((float)cs[2]) * kMargin,
+                    sqrtf((float)cs[3]) * kMargin);
+  }
+}
+
 __device__ bool choose_pivot(cg::cluster_group &cl, const Team &tm, int j0, int64_t n, const double *vno,
                              const int *flago, int *doneo, int *perm, int *posof, unsigned long long *cand,
                              int *s_res) {
@@ -837,7 +861,16 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
   __syncthreads();
 
   // ---- initial column norms and the first pivot
-  {
+  if (a.colsq) {  // given by the caller: no pass over A, no reduction
+    if (tid < kColT) nat_from_colsq<kColT>(a, nat);
+    for (int lc = tid; lc < tm.nown; lc += kCT) {
+      const double v = a.colsq[tm.rank + tm.S * lc];
+      vno[lc] = v;
+      vrefo[lc] = v;
+    }
+    __syncthreads();
+    choose_pivot(cl, tm, 0, n, vno, flago, doneo, perm, posof, cand, &s_res);
+  } else {
     PT *rp = reinterpret_cast<PT *>(red) + (size_t)par * L;
     if (tid < kColT)  // the layout of the A^T y passes, which use the norm bounds it leaves in nat
       ccolsum<AT, true, kColT>(a, As, ncache, r0, 0, nrows, ys, cscr, nat, rp);
@@ -1265,6 +1298,7 @@ bool qrp_cluster(const AT *A, int64_t m, int64_t n, int64_t lda, int k, double *
   a.ldq = ldq;
   a.piv = piv;
   a.rdiag = rdiag;
+  a.colsq = (es == 4 && a.vec4) ? w->colsq : nullptr;
   if (C > 1 && (*err = cudaMemsetAsync(w->bar, 0, 3 * sizeof(unsigned), s)) != cudaSuccess) return true;
 
   cudaLaunchConfig_t cfg = {};

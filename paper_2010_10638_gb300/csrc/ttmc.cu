@@ -21,6 +21,7 @@
 #include <algorithm>
 #include <cstdlib>
 
+#include "dfloat.cuh"
 #include "internal.cuh"
 
 namespace tk {
@@ -48,6 +49,8 @@ struct TtmcParams {
   uint32_t *err;         // the context's error word (bounded waits that gave up)
   const uint32_t *fptr;  // fiber form: [F+1] first nonzero of each fiber (positions above are fibers)
   const uint32_t *fmid;  // fiber form: [F] index of the first remaining mode of each fiber
+  float2 *sq_part;       // pipelined form: [blocks][P] column sums of squares of the whole rows each
+                         // block wrote (double-float pairs), nullptr: not formed
 };
 
 // Slice structure of the tile [e, e + nt) of sorted positions, kb = slice of position e.
@@ -263,22 +266,87 @@ __global__ void __launch_bounds__(kTtmcWarps * 32) ttmc_fast_kernel(const TtmcPa
 }
 
 // ============================================================================ pipelined form
+// s += (x.x + x.y): TwoSum of the high parts, every rounding error into the low part
+__device__ __forceinline__ void sq_add(DF &s, float2 x) {
+  const float t = s.hi + x.x, bp = t - s.hi;
+  s.lo += ((s.hi - (t - bp)) + (x.x - bp)) + x.y;
+  s.hi = t;
+}
+
 // The arithmetic of ttmc_fast_kernel (order 3: one left mode) with the global latency of
 // each tile shortened: the slice offsets, indices and values of tile t+1 are loaded into
 // registers while tile t is staged and computed, so a tile waits on one round trip (the
 // L1-cached factor-row gathers) instead of three chained ones.
-template <int PL, int RB, int TA, int TB>
-__global__ void __launch_bounds__(kTtmcWarps * 32) ttmc_pipe_kernel(const TtmcParams p) {
+// SQ form of the pipelined TTMc, after a warp's last tile: the rows it wrote whole (slices
+// kfirst .. kfirst + nrows - 1), read back through L2 (lane l: columns CPL l .. CPL l + CPL - 1),
+// their exact squares summed in double-float pairs into the warp's staging area (warp w's
+// at smem + w * ws floats).  The last warp of the block to arrive adds the eight warps'
+// pairs in warp order to sq_part[block]: no block barrier, so warps without a unit leave early.
+template <int P>
+__device__ __forceinline__ void sq_rows_finish(const TtmcParams &p, float *smem, int ws, uint32_t kfirst,
+                                               uint32_t nrows, unsigned *arrived) {
+  constexpr int CPL = P / 32;
+  static_assert(CPL % 2 == 0, "column pairs per lane");
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  DF q[CPL];
+  __syncwarp();  // this warp's rows of Y are visible to all its lanes
+#pragma unroll 1
+  for (uint32_t r = 0; r < nrows; ++r) {
+    const float2 *y = reinterpret_cast<const float2 *>(p.Y + (size_t)__ldg(p.sid + kfirst + r) * P + lane * CPL);
+    float2 v[CPL / 2];
+#pragma unroll
+    for (int c = 0; c < CPL / 2; ++c) v[c] = __ldcg(y + c);
+#pragma unroll
+    for (int c = 0; c < CPL / 2; ++c) {
+      df_fma(q[2 * c], v[c].x, v[c].x, 0.f);
+      df_fma(q[2 * c + 1], v[c].y, v[c].y, 0.f);
+    }
+  }
+  float2 *mine = reinterpret_cast<float2 *>(smem + w * ws);  // the tiles are done: the area is free
+#pragma unroll
+  for (int c = 0; c < CPL; ++c) mine[lane * CPL + c] = make_float2(q[c].hi, q[c].lo);
+  __syncwarp();  // the warp's pairs are written ...
+  unsigned before = 0;
+  if (lane == 0) {
+    __threadfence_block();  // ... and ordered before its arrival
+    before = atomicAdd(arrived, 1u);
+    if (before == kTtmcWarps - 1) __threadfence_block();  // every arrival's pairs before the reads
+  }
+  before = __shfl_sync(0xffffffffu, before, 0);  // (and the warp's lanes after lane 0's fence)
+  if (before != kTtmcWarps - 1) return;
+  for (int c = lane; c < P; c += 32) {
+    DF t;
+    for (int ww = 0; ww < kTtmcWarps; ++ww) sq_add(t, reinterpret_cast<const float2 *>(smem + ww * ws)[c]);
+    p.sq_part[(size_t)blockIdx.x * P + c] = make_float2(t.hi, t.lo);
+  }
+}
+
+template <int PL, int RB, int TA, int TB, bool SQ>
+__device__ __forceinline__ void ttmc_pipe_body(const TtmcParams &p) {
   constexpr int G = (PL / TA) * (RB / TB);
   constexpr int NG = 32 / G;
   static_assert(G * NG == 32, "group size must divide the warp");
   static_assert(PL % 4 == 0 && RB % 4 == 0, "16-byte row pieces");
+  static_assert(!SQ || PL * RB * 2 <= 32 * (PL + RB), "SQ: a warp's pairs fit its staging area");
   extern __shared__ float4 smem_f4[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   float *xa = reinterpret_cast<float *>(smem_f4) + w * 32 * (PL + RB);
   float *bb = xa + 32 * PL;
+  // SQ: a unit with slot < 0 holds whole slices only, the consecutive slices from its first,
+  // kfirst, to the one that starts where it ends (kb after its last tile); their rows'
+  // squares are summed after the last tile
+  uint32_t kfirst = 0, nrows = 0;
+  __shared__ unsigned s_sq_arrived;  // SQ: warps whose pairs are in their staging areas
+  if constexpr (SQ) {
+    if (threadIdx.x == 0) s_sq_arrived = 0u;
+    __syncthreads();
+  }
   const int64_t u = (int64_t)blockIdx.x * kTtmcWarps + w;
-  if (u >= p.n_units) return;
+  if (u >= p.n_units) {
+    if constexpr (SQ) sq_rows_finish<PL * RB>(p, reinterpret_cast<float *>(smem_f4), 32 * (PL + RB), 0u, 0u, &s_sq_arrived);
+    return;
+  }
+  {
   const float *UA = static_cast<const float *>(p.U[0]);
   const float *UB = static_cast<const float *>(p.U[1]);
   const uint32_t *idxA = p.idx[0];
@@ -395,6 +463,29 @@ __global__ void __launch_bounds__(kTtmcWarps * 32) ttmc_pipe_kernel(const TtmcPa
     ia = ian;
     ib = ibn;
   }
+  if constexpr (SQ) {  // the unit's index and tables are read again: nothing more stays live
+    const int64_t uu = (int64_t)blockIdx.x * kTtmcWarps + (threadIdx.x >> 5);
+    if (__ldg(p.unit_slot + uu) < 0) {
+      kfirst = __ldg(p.unit_k0 + uu);
+      nrows = kb - kfirst;
+    }
+  }
+  }
+  if constexpr (SQ) {
+    sq_rows_finish<PL * RB>(p, reinterpret_cast<float *>(smem_f4), 32 * (PL + RB), kfirst, nrows, &s_sq_arrived);
+  }
+}
+
+template <int PL, int RB, int TA, int TB>
+__global__ void __launch_bounds__(kTtmcWarps * 32) ttmc_pipe_kernel(const TtmcParams p) {
+  ttmc_pipe_body<PL, RB, TA, TB, false>(p);
+}
+
+// The same, also forming the column sums of squares of the rows it writes (p.sq_part, one
+// row of P pairs per block); held to 64 registers, the occupancy of the plain form.
+template <int PL, int RB, int TA, int TB>
+__global__ void __launch_bounds__(kTtmcWarps * 32, 4) ttmc_pipe_sq_kernel(const TtmcParams p) {
+  ttmc_pipe_body<PL, RB, TA, TB, true>(p);
 }
 
 // ============================================================================ fiber form
@@ -1330,11 +1421,13 @@ __global__ void __launch_bounds__(kTtmcWarps * 32) ttmc_generic_kernel(const Ttm
 // Rows of slices split over several units: block (l, c) sums the partial rows of long
 // slice l for columns [32c, 32c + 32).  Warp w adds the pieces w, w + 8, ... (four loads in
 // flight), then the eight warp sums are added in warp order: a fixed order, so Y is
-// reproducible, and a slice cut into thousands of pieces is summed by many blocks.
+// reproducible, and a slice cut into thousands of pieces is summed by many blocks.  With
+// `sq` given, the exact square of each finished entry goes to sq[l * P + c] as a pair.
 constexpr int kFixWarps = 8;
 __global__ void __launch_bounds__(kFixWarps * 32) ttmc_fixup_kernel(const uint32_t *long_k, const uint32_t *long_u0,
                                                                      const uint32_t *long_np, const uint32_t *sid,
-                                                                     const float *carry, float *Y, int64_t P) {
+                                                                     const float *carry, float *Y, int64_t P,
+                                                                     float2 *sq) {
   __shared__ float part[kFixWarps][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t l = blockIdx.x, c = (int64_t)blockIdx.y * 32 + lane;
@@ -1359,13 +1452,88 @@ __global__ void __launch_bounds__(kFixWarps * 32) ttmc_fixup_kernel(const uint32
 #pragma unroll
     for (int k = 1; k < kFixWarps; ++k) t += part[k][lane];
     Y[(size_t)row * P + c] = t;
+    if (sq) {
+      const float t2 = t * t;
+      sq[(size_t)l * P + c] = make_float2(t2, fmaf(t, t, -t2));
+    }
   }
 }
 
 static void launch_fixup(const uint32_t *long_k, const uint32_t *long_u0, const uint32_t *long_np, int64_t n_long,
-                         const uint32_t *sid, const float *carry, float *Y, int64_t P, cudaStream_t s) {
+                         const uint32_t *sid, const float *carry, float *Y, int64_t P, cudaStream_t s,
+                         float2 *sq = nullptr) {
   const dim3 grid((unsigned)n_long, (unsigned)((P + 31) / 32));
-  ttmc_fixup_kernel<<<grid, kFixWarps * 32, 0, s>>>(long_k, long_u0, long_np, sid, carry, Y, P);
+  ttmc_fixup_kernel<<<grid, kFixWarps * 32, 0, s>>>(long_k, long_u0, long_np, sid, carry, Y, P, sq);
+  ::tk::count_launch();
+}
+
+// Column sums of squares of Y_(n) from the pairs of the pipelined TTMc and the fixup
+// (`rows` rows of P pairs), in two levels within one launch.  Block (g, h) adds rows
+// [64h, 64h + 64) of columns [32g, 32g + 32): warp w the rows 64h + w, 64h + w + 8, ...
+// (all eight loads in flight), then the warp sums in warp order, to chunk[h].  The last
+// block of column group g to finish (a counter, which that block resets) adds the chunks
+// in order and the warps' sums in FP64.  A fixed order: the norms are reproducible.
+constexpr int kSqRows = 64, kSqW = 8;
+__global__ void __launch_bounds__(kSqW * 32) ttmc_colsq_kernel(const float2 *part, int64_t rows, int64_t P,
+                                                               float2 *chunk, unsigned *cnt, double *colsq) {
+  __shared__ float2 ws[kSqW][32];
+  __shared__ int last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t c = (int64_t)blockIdx.x * 32 + lane;
+  const int64_t r0 = (int64_t)blockIdx.y * kSqRows + warp;
+  DF t;
+  if (c < P) {
+    float2 v[kSqRows / kSqW];
+#pragma unroll
+    for (int u = 0; u < kSqRows / kSqW; ++u) {
+      const int64_t r = r0 + u * kSqW;
+      v[u] = r < rows ? __ldcg(part + (size_t)r * P + c) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < kSqRows / kSqW; ++u) sq_add(t, v[u]);
+  }
+  ws[warp][lane] = make_float2(t.hi, t.lo);
+  __syncthreads();
+  if (warp == 0) {
+    DF b;
+    for (int w = 0; w < kSqW; ++w) sq_add(b, ws[w][lane]);
+    if (c < P) chunk[(size_t)blockIdx.y * P + c] = make_float2(b.hi, b.lo);
+    __threadfence();  // the chunk is visible before the counter says so
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(cnt + blockIdx.x, 1u) == gridDim.y - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int nch = (int)gridDim.y;
+  DF f;
+  if (c < P) {
+    int h = warp;
+    for (; h + 3 * kSqW < nch; h += 4 * kSqW) {
+      float2 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = __ldcg(chunk + (size_t)(h + u * kSqW) * P + c);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) sq_add(f, v[u]);
+    }
+    for (; h < nch; h += kSqW) sq_add(f, __ldcg(chunk + (size_t)h * P + c));
+  }
+  ws[warp][lane] = make_float2(f.hi, f.lo);
+  __syncthreads();
+  if (warp == 0 && c < P) {
+    double v = 0.0;
+    for (int w = 0; w < kSqW; ++w) v += (double)ws[w][lane].x + (double)ws[w][lane].y;
+    colsq[c] = v;
+  }
+  if (threadIdx.x == 0) cnt[blockIdx.x] = 0u;  // ready for the next launch
+}
+
+// rows of pairs in `part`, then the chunk sums after them (sq_elems covers both)
+static int64_t colsq_chunks(int64_t rows) { return (rows + kSqRows - 1) / kSqRows; }
+
+static void launch_colsq(float2 *part, int64_t rows, int64_t P, unsigned *cnt, double *colsq, cudaStream_t s) {
+  const dim3 grid((unsigned)((P + 31) / 32), (unsigned)colsq_chunks(rows));
+  ttmc_colsq_kernel<<<grid, kSqW * 32, 0, s>>>(part, rows, P, part + (size_t)rows * P, cnt, colsq);
   ::tk::count_launch();
 }
 
@@ -1449,11 +1617,16 @@ static bool dispatch_bf16(const TtmcParams &p, cudaStream_t s, cudaError_t *err)
 
 template <int PL, int RB, int TA, int TB>
 static cudaError_t run_pipe(const TtmcParams &p, cudaStream_t s) {
+  // the norm-forming kernel (p.sq_part given) exists where the pairs stay small: P_n <= 256
+  constexpr bool kSqShape = PL * RB <= 256;
+  if (p.sq_part && !kSqShape) return cudaErrorInvalidValue;
   const size_t smem = (size_t)kTtmcWarps * 32 * (PL + RB) * sizeof(float);
   auto kern = ttmc_pipe_kernel<PL, RB, TA, TB>;
+  if constexpr (kSqShape)
+    if (p.sq_part) kern = ttmc_pipe_sq_kernel<PL, RB, TA, TB>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const unsigned blocks = (unsigned)((p.n_units + kTtmcWarps - 1) / kTtmcWarps);
+  const unsigned blocks = (unsigned)ttmc_pipe_blocks(p.n_units);
   kern<<<blocks, kTtmcWarps * 32, smem, s>>>(p);
   ::tk::count_launch();
   return cudaGetLastError();
@@ -1487,6 +1660,8 @@ static bool dispatch_fibsum(const TtmcParams &p, float *T, int64_t nnz, cudaStre
 }
 
 static bool dispatch_pipe(const TtmcParams &p, cudaStream_t s, cudaError_t *err);
+
+int64_t ttmc_pipe_blocks(int64_t units) { return (units + kTtmcWarps - 1) / kTtmcWarps; }
 
 // shapes (first rank, last rank) of the pipelined kernel below
 static bool pipe_shape(int PL, int RB) {
@@ -1565,9 +1740,14 @@ static bool fused_fibers() {
   return e && e[0] == '1';
 }
 
+// With `colsq` given, the pipelined FP32 forms also write the column sums of squares of Y
+// there (*norms true); every other form leaves *norms false.
 static tucker_status ttmc_impl(Ctx *c, int mode, float *Y, const float *val, const float *const *Uf,
-                               cudaStream_t s) {
+                               cudaStream_t s, double *colsq = nullptr, bool *norms = nullptr) {
   const ModeCopy &mc = c->mode[mode];
+  if (norms) *norms = false;
+  // per-block pairs of P columns for each of the 8 warps: formed where that stays small
+  const bool want_sq = colsq && norms && c->sq_part && c->sq_cnt && mc.P <= 256;
   const bool bf16 = !Uf && (c->flags & TUCKER_F_BF16_FACTORS) != 0;
   TtmcParams p{};
   p.nother = mc.nother;
@@ -1657,9 +1837,18 @@ static tucker_status ttmc_impl(Ctx *c, int mode, float *Y, const float *val, con
       r.idx[1 - ft] = c->fib_iota;
       r.U[1 - ft] = c->fib_T;
       r.val = c->fib_ones;
+      const int64_t nb = ttmc_pipe_blocks(r.n_units);
+      const bool sq = want_sq && (nb + mc.fn_long + colsq_chunks(nb + mc.fn_long)) * mc.P <= c->sq_elems;
+      if (sq) r.sq_part = c->sq_part;
       dispatch_pipe(r, s, &err);  // covers the shape (checked above)
       TK_CUDA(err);
-      if (mc.fn_long > 0) launch_fixup(mc.flong_k, mc.flong_u0, mc.flong_np, mc.fn_long, mc.sid, c->carry, Y, mc.P, s);
+      if (mc.fn_long > 0)
+        launch_fixup(mc.flong_k, mc.flong_u0, mc.flong_np, mc.fn_long, mc.sid, c->carry, Y, mc.P, s,
+                     sq ? c->sq_part + nb * mc.P : nullptr);
+      if (sq) {
+        launch_colsq(c->sq_part, nb + mc.fn_long, mc.P, c->sq_cnt, colsq, s);
+        *norms = true;
+      }
       if (mc.n_empty > 0) {
         ttmc_zero_rows_kernel<<<(unsigned)std::min<int64_t>(mc.n_empty, 65535), 256, 0, s>>>(mc.empty, mc.n_empty,
                                                                                             Y, mc.P);
@@ -1669,6 +1858,8 @@ static tucker_status ttmc_impl(Ctx *c, int mode, float *Y, const float *val, con
       return TUCKER_OK;
     }
   }
+  int64_t sq_rows = 0;      // rows of pairs the pipelined form left (0: none)
+  float2 *sq_fix = nullptr;  // where the fixup puts the squares of the split slices' rows
   if (mc.n_units > 0) {
     cudaError_t err = cudaSuccess;
     bool done = false;
@@ -1680,15 +1871,30 @@ static tucker_status ttmc_impl(Ctx *c, int mode, float *Y, const float *val, con
       } else {
         done = dispatch_bf16(p, s, &err);
       }
-    } else if (!(c->flags & TUCKER_F_UNPIPELINED))
+    } else if (!(c->flags & TUCKER_F_UNPIPELINED)) {
+      const int64_t nb = ttmc_pipe_blocks(p.n_units);
+      const bool sq = want_sq && pipe_shape(p.R[0], p.R[1]) && p.nother == 2 &&
+                      (nb + mc.n_long + colsq_chunks(nb + mc.n_long)) * mc.P <= c->sq_elems;
+      if (sq) p.sq_part = c->sq_part;
       done = dispatch_pipe(p, s, &err);
+      if (done && sq) {
+        sq_rows = nb + mc.n_long;
+        sq_fix = c->sq_part + nb * mc.P;
+      }
+      p.sq_part = nullptr;
+    }
     if (!done) done = bf16 ? dispatch_fast<__nv_bfloat16>(p, s, &err) : dispatch_fast<float>(p, s, &err);
     if (!done) err = bf16 ? run_generic<__nv_bfloat16>(p, s) : run_generic<float>(p, s);
     TK_CUDA(err);
   }
   if (mc.n_long > 0) {
-    launch_fixup(mc.long_k, mc.long_u0, mc.long_np, mc.n_long, mc.sid, c->carry, Y, mc.P, s);
+    launch_fixup(mc.long_k, mc.long_u0, mc.long_np, mc.n_long, mc.sid, c->carry, Y, mc.P, s, sq_fix);
     TK_CUDA(cudaGetLastError());
+  }
+  if (sq_rows > 0) {
+    launch_colsq(c->sq_part, sq_rows, mc.P, c->sq_cnt, colsq, s);
+    TK_CUDA(cudaGetLastError());
+    *norms = true;
   }
   if (mc.n_empty > 0) {
     ttmc_zero_rows_kernel<<<(unsigned)std::min<int64_t>(mc.n_empty, 65535), 256, 0, s>>>(mc.empty, mc.n_empty, Y,
@@ -1731,6 +1937,10 @@ void make_factor_maps(Ctx *c) {
 
 tucker_status launch_ttmc(Ctx *c, int mode, float *Y, cudaStream_t s) {
   return ttmc_impl(c, mode, Y, nullptr, nullptr, s);
+}
+
+tucker_status launch_ttmc_norms(Ctx *c, int mode, float *Y, double *colsq, bool *formed, cudaStream_t s) {
+  return ttmc_impl(c, mode, Y, nullptr, nullptr, s, colsq, formed);
 }
 
 tucker_status launch_ttmc_ex(Ctx *c, int mode, float *Y, const float *val, const float *const *Uf, cudaStream_t s) {

@@ -28,11 +28,12 @@ TUCKER_F_QRP_DIRECT = 0x2
 TUCKER_F_HOST_INPUT = 0x4
 TUCKER_F_FIT_DEVICE = 0x8
 TUCKER_F_UNPIPELINED = 0x20
+TUCKER_F_TTMC_NORMS = 0x40
 
 STATUS = {0: "TUCKER_OK", 1: "TUCKER_EINVAL", 2: "TUCKER_ERANK", 3: "TUCKER_ENOMEM", 4: "TUCKER_ECUDA",
           5: "TUCKER_ETIMEOUT", 6: "TUCKER_ESTATE"}
 
-EXPORTS = ["tucker_init", "ttmc_mode", "qrp_leading", "qrp_leading_work_bytes", "hooi_iter", "core_tensor",
+EXPORTS = ["tucker_init", "ttmc_mode", "ttmc_mode_norms", "qrp_leading", "qrp_leading_work_bytes", "hooi_iter", "core_tensor",
            "tucker_get_factor", "tucker_set_factor", "tucker_loss_grad", "tucker_nnz", "tucker_norm2",
            "tucker_sync_status", "tucker_free", "tucker_status_str", "tucker_last_error", "tucker_set_profiling",
            "tucker_phase_times", "tucker_kernel_launches", "qrp_leading_noalloc", "qrp_leading_noalloc_max_bytes",
@@ -64,6 +65,7 @@ def load(path: str = LIB_PATH):
                                          ctypes.c_int, ctypes.c_size_t, ctypes.c_double)
     lib.tucker_init.argtypes = [P(vp), cint, P(i64), i64, vp, vp, P(cint), vp, u64, u32, vp]
     lib.ttmc_mode.argtypes = [vp, cint, vp, vp]
+    lib.ttmc_mode_norms.argtypes = [vp, cint, vp, vp, vp]
     lib.qrp_leading.argtypes = [vp, i64, i64, i64, cint, vp, vp, vp, vp, csz, vp]
     lib.qrp_leading_work_bytes.argtypes = [i64, i64, cint]
     lib.qrp_leading_work_bytes.restype = csz
@@ -172,7 +174,7 @@ def tucker_lib_setup(device: int | None = None) -> None:
 
 
 def tucker_init(dims, coords, vals, ranks, U0=None, seed: int = 0, bf16: bool = False, direct: bool = False,
-                fit_device: bool = False, unpipelined: bool = False,
+                fit_device: bool = False, unpipelined: bool = False, ttmc_norms: bool = False,
                 stream=None) -> Context:
     """coords: int32/uint32 [N, nnz]; vals: float32 [nnz]; U0: list of N float64 [I_m, R_m] or None.
     CUDA tensors are passed as device pointers; CPU tensors / numpy arrays as host pointers
@@ -181,7 +183,7 @@ def tucker_init(dims, coords, vals, ranks, U0=None, seed: int = 0, bf16: bool = 
     N = len(dims)
     flags = (TUCKER_F_BF16_FACTORS if bf16 else 0) | (TUCKER_F_QRP_DIRECT if direct else 0) | (
         TUCKER_F_FIT_DEVICE if fit_device else 0) | (
-        TUCKER_F_UNPIPELINED if unpipelined else 0)
+        TUCKER_F_UNPIPELINED if unpipelined else 0) | (TUCKER_F_TTMC_NORMS if ttmc_norms else 0)
     on_host = not (isinstance(coords, torch.Tensor) and coords.is_cuda)
     keep = []
     if on_host:
@@ -225,6 +227,21 @@ def ttmc_mode(ctx: Context, mode: int, Y: torch.Tensor | None = None, stream=Non
     _dev(Y, torch.float32, "Y")
     _check(load().ttmc_mode(ctx.handle, int(mode), Y.data_ptr(), _stream(stream)), "ttmc_mode", ctx)
     return Y
+
+
+def ttmc_mode_norms(ctx: Context, mode: int, Y: torch.Tensor | None = None, colsq: torch.Tensor | None = None,
+                    stream=None):
+    """ttmc_mode plus the column sums of squares of Y_(n) (float64 [P_n]) formed as Y is
+    written.  Returns (Y, colsq)."""
+    if Y is None:
+        Y = torch.empty((ctx.dims[mode], ctx.P(mode)), dtype=torch.float32, device="cuda")
+    if colsq is None:
+        colsq = torch.empty(ctx.P(mode), dtype=torch.float64, device="cuda")
+    _dev(Y, torch.float32, "Y")
+    _dev(colsq, torch.float64, "colsq")
+    _check(load().ttmc_mode_norms(ctx.handle, int(mode), Y.data_ptr(), colsq.data_ptr(), _stream(stream)),
+           "ttmc_mode_norms", ctx)
+    return Y, colsq
 
 
 def hooi_iter(ctx: Context, fit_out: torch.Tensor | None = None, stream=None):
