@@ -288,6 +288,17 @@ TUCKER_API double tucker_fp32_fma_tflops(int iters, void *stream);
 TUCKER_API uint64_t tucker_kernel_launches(void);
 
 /*
+ * tucker_check_site — for the checked build of the library (the cluster QRP compiled with
+ * TUCKER_QRP_CHECKED: every index of its shared, distributed-shared and global arrays is
+ * compared with the array's length; one outside is replaced by 0 and its site recorded,
+ * and the launch's error word gets a check bit, so hooi_iter returns TUCKER_ECUDA and the
+ * standalone QRP's status query TUCKER_ECUDA): the number of the first site whose index
+ * fell outside, 0 when none did.  Synchronises the current device.  Returns -1 in the
+ * normal build (no checks compiled in), -2 if a CUDA call failed.
+ */
+TUCKER_API int32_t tucker_check_site(void);
+
+/*
  * Self-test of the bounded device-side waits (no counterpart in the paper): one block
  * polls a flag that nothing sets, with the bounded loop of the QRP grid barrier (at most
  * max_polls polls about 100 ns apart), gives up and latches the timeout bit in the

@@ -93,6 +93,10 @@ static tucker_status check_err_word(Ctx *c, cudaStream_t s) {
       c->last_error = "a kernel was launched in a shape other than the one it was planned for";
       return TUCKER_ECUDA;
     }
+    if (bits & kErrCheck) {
+      c->last_error = "checked build: an index fell outside its array (tucker_check_site names it)";
+      return TUCKER_ECUDA;
+    }
     c->last_error = "device-side input check failed";
     return TUCKER_EINVAL;
   }
@@ -428,6 +432,8 @@ int tucker_phase_times(tucker_ctx *h, float *ms, int cap) {
 }
 
 uint64_t tucker_kernel_launches(void) { return tk::g_launches.load(); }
+
+int32_t tucker_check_site(void) { return tk::qrp_check_site(); }
 
 int tucker_mode_info(const tucker_ctx *h, int mode, int64_t *out, int cap) {
   if (!h || !out || cap < 0 || mode < 0 || mode >= h->c.N) return -1;

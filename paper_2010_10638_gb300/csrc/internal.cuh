@@ -19,6 +19,7 @@ constexpr uint32_t kErrCoord = 1u;    // a coordinate >= its dimension
 constexpr uint32_t kErrValue = 2u;    // a non-finite value
 constexpr uint32_t kErrTimeout = 4u;  // a bounded device-side wait gave up
 constexpr uint32_t kErrLaunch = 8u;   // a kernel found its launch shape different from its plan
+constexpr uint32_t kErrCheck = 16u;   // checked build: an index fell outside its array
 
 // Per-mode sorted copy of the nonzeros (a CSF root level over the non-empty slices)
 // and the work-unit table of the TTMc kernel.
@@ -215,6 +216,7 @@ tucker_status launch_ttmc(Ctx *c, int mode, float *Y, cudaStream_t s);
 // pipelined FP32 form runs (*formed true), at no extra pass over Y; *formed false otherwise.
 tucker_status launch_ttmc_norms(Ctx *c, int mode, float *Y, double *colsq, bool *formed, cudaStream_t s);
 int64_t ttmc_pipe_blocks(int64_t units);  // blocks of a pipelined TTMc launch over `units` units
+int32_t qrp_check_site();                 // checked build: first index check that failed (0: none); -1 otherwise
 // TMA descriptors of the BF16 factor copies (host only; no device work)
 void make_factor_maps(Ctx *c);
 // 0, 1, ..., n-1 and n ones (the index and value streams of the fiber form's update pass)

@@ -97,6 +97,26 @@ struct CArgs {
                         // float4 only), or nullptr: the first pass over A forms them
 };
 
+// Checked build (TUCKER_QRP_CHECKED): QX(i, len, site) is i when 0 <= i < len; otherwise it
+// records the site and gives 0, so that the access stays inside its array.  Each block
+// reports a recorded site through the launch's error word (kErrCheck) as it leaves.  In
+// the normal build QX(i, len, site) is i itself and nothing else changes.
+#ifdef TUCKER_QRP_CHECKED
+__device__ unsigned g_qc_site;  // first site whose index fell outside its array (0: none)
+__device__ __forceinline__ int64_t qc_index(int64_t i, int64_t len, unsigned site) {
+  if (i >= 0 && i < len) return i;
+  atomicCAS(&g_qc_site, 0u, site);
+  return 0;
+}
+#define QX(i, len, site) qc_index((int64_t)(i), (int64_t)(len), (site))
+__device__ __forceinline__ void qc_report(uint32_t *err) {
+  if (threadIdx.x == 0 && *(volatile unsigned *)&g_qc_site) atomicOr(err, kErrCheck);
+}
+#else
+#define QX(i, len, site) (i)
+__device__ __forceinline__ void qc_report(uint32_t *) {}
+#endif
+
 // Dynamic shared memory of one block; the same arithmetic on host and device.
 struct CLayout {
   size_t Fo, vno, vrefo, ajo, svo, svs, flago, doneo, red, Ts, Vt, Ms, su, Vs, red4, cscr, nat, ys, perm, posof, cand,
@@ -327,7 +347,7 @@ __device__ bool allreduce(const CArgs &a, cg::cluster_group &cl, Team &tm, PT *m
   };
   cl.sync();  // every block of the cluster has written its partials
   if (a.nclusters == 1) {
-    for (int t = threadIdx.x; t < need; t += kCT) store(t, Part<PT>::val(peer_sum(cl, mine, tm.S, entry(t))));
+    for (int t = threadIdx.x; t < need; t += kCT) store(t, Part<PT>::val(peer_sum(cl, mine, tm.S, QX(entry(t), L, 1))));
     __syncthreads();
     return true;  // `mine` alternates between two buffers: the next write cannot race these reads
   }
@@ -337,7 +357,7 @@ __device__ bool allreduce(const CArgs &a, cg::cluster_group &cl, Team &tm, PT *m
   const int q0 = (int)tm.rank * per, q1 = min(L, q0 + per);
   bool wrote = false;
   for (int q = q0 + threadIdx.x; q < q1; q += kCT) {
-    slot[q] = peer_sum(cl, mine, tm.S, q);
+    slot[q] = peer_sum(cl, mine, tm.S, QX(q, L, 2));
     wrote = true;
   }
   if (wrote) __threadfence();
@@ -361,7 +381,7 @@ __device__ bool allreduce(const CArgs &a, cg::cluster_group &cl, Team &tm, PT *m
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
       const int cc = 16 * h + u;
-      x[u] = (cc < a.nclusters) ? __ldcg(base + (size_t)cc * L + q) : Part<PT>::zero();
+      x[u] = (cc < a.nclusters) ? __ldcg(base + (size_t)cc * L + QX(q, L, 3)) : Part<PT>::zero();
     }
     scratch[idx] = ptree<16>(x);
   }
@@ -537,7 +557,7 @@ __device__ void ccolsum(const CArgs &a, const AT *As, int64_t ncache, int64_t r0
                              nrl, y2, d[0], d[1], d[2], d[3]);
           }
           if (nat && act)
-            nat4[it * NT + threadIdx.x] = make_float4(sqrtf(fmaxf(d[0].hi, 0.f)) * kMargin, sqrtf(fmaxf(d[1].hi, 0.f)) * kMargin,
+            nat4[QX(it * NT + threadIdx.x, ((nq + cw - 1) / cw) * NT, 4)] = make_float4(sqrtf(fmaxf(d[0].hi, 0.f)) * kMargin, sqrtf(fmaxf(d[1].hi, 0.f)) * kMargin,
                                                       sqrtf(fmaxf(d[2].hi, 0.f)) * kMargin, sqrtf(fmaxf(d[3].hi, 0.f)) * kMargin);
 #pragma unroll
           for (int h = 0; h < 2; ++h) {  // two columns of the four at a time through the scratch
@@ -578,7 +598,7 @@ __device__ void ccolsum(const CArgs &a, const AT *As, int64_t ncache, int64_t r0
         for (int64_t q0 = 0, it = 0; q0 < nq; q0 += cw, ++it) {
           const int64_t qc = q0 + cq;
           const bool mine = act && qc < nq;
-          const float4 nb = mine ? nat4[it * NT + threadIdx.x] : make_float4(0.f, 0.f, 0.f, 0.f);
+          const float4 nb = mine ? nat4[QX(it * NT + threadIdx.x, ((nq + cw - 1) / cw) * NT, 5)] : make_float4(0.f, 0.f, 0.f, 0.f);
           const float s1[4] = {off_s1(nb.x * sy), off_s1(nb.y * sy), off_s1(nb.z * sy), off_s1(nb.w * sy)};
           OffAcc d[4];
 #pragma unroll
@@ -687,8 +707,8 @@ __device__ void nat_from_colsq(const CArgs &a, float *nat) {
   for (int64_t q0 = 0, it = 0; q0 < nq; q0 += cw, ++it) {
     const int64_t qc = q0 + cq;
     if (qc >= nq) continue;  // no pass reads these
-    const double *cs = a.colsq + 4 * qc;
-    nat4[it * NT + threadIdx.x] =
+    const double *cs = a.colsq + QX(4 * qc, a.n - 3, 6);
+    nat4[QX(it * NT + threadIdx.x, ((nq + cw - 1) / cw) * NT, 7)] =
         make_float4(sqrtf((float)cs[0]) * kMargin, sqrtf((float)cs[1]) * kMargin, sqrtf((float)cs[2]) * kMargin,
                     sqrtf((float)cs[3]) * kMargin);
   }
@@ -764,6 +784,7 @@ __device__ bool choose_pivot(cg::cluster_group &cl, const Team &tm, int j0, int6
 }
 
 __device__ void cbail(const CArgs &a) {
+  qc_report(a.err);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     const double qnan = __longlong_as_double(0x7ff8000000000000ll);
     if (a.rdiag)
@@ -864,7 +885,7 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
   if (a.colsq) {  // given by the caller: no pass over A, no reduction
     if (tid < kColT) nat_from_colsq<kColT>(a, nat);
     for (int lc = tid; lc < tm.nown; lc += kCT) {
-      const double v = a.colsq[tm.rank + tm.S * lc];
+      const double v = a.colsq[QX(tm.rank + tm.S * lc, n, 8)];
       vno[lc] = v;
       vrefo[lc] = v;
     }
@@ -888,36 +909,38 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
 
   const double tol = sqrt(DBL_EPSILON);
   for (int j = 0; j < k; ++j) {
-    const int c0 = perm[j];
+    const int c0 = (int)QX(perm[j], n, 9);
     const bool owner = j >= r0 && j < r1;
     if (tid < j) {  // F[c0, :j] from the block that owns column c0
-      const double *pF = cl.map_shared_rank(Fo, (unsigned)(c0 % (int)tm.S));
-      s_f[tid] = pF[(int64_t)tid * no + c0 / (int)tm.S];
+      const double *pF = cl.map_shared_rank(Fo, (unsigned)QX(c0 % (int)tm.S, tm.S, 10));
+      s_f[QX(tid, 64, 11)] = pF[QX((int64_t)tid * no + c0 / (int)tm.S, (int64_t)k * no, 12)];
     }
     for (int lc = tid; lc < tm.nown; lc += kCT)  // A[j, :] of this block's columns, used after the reduction
-      ajo[lc] = (double)__ldg(A + (int64_t)j * a.lda + tm.rank + (int64_t)tm.S * lc);
+      ajo[QX(lc, no, 13)] = (double)__ldg(A + QX((int64_t)j * a.lda + tm.rank + (int64_t)tm.S * lc, m * a.lda, 14));
     __syncthreads();
     // ---- rows: y = A[:, c0] - V[:, :j] F[c0, :j]^T (zero above row j)
     double s2 = 0.0;
     for (int64_t li = tid; li < nrows; li += kCT) {
       const int64_t i = r0 + li;
-      double *vr = Vs + li * kp;
+      double *vr = Vs + QX(li * kp, a.rows_per * kp, 15);
       if (i < j) {
-        vr[j] = 0.0;
-        if constexpr (sizeof(AT) == 4) reinterpret_cast<float2 *>(a.Q)[i * a.ldq + j] = make_float2(0.f, 0.f);
+        vr[QX(j, kp, 16)] = 0.0;
+        if constexpr (sizeof(AT) == 4)
+          reinterpret_cast<float2 *>(a.Q)[QX(i * a.ldq + j, m * a.ldq, 17)] = make_float2(0.f, 0.f);
         continue;
       }
-      double y = li < ncache ? (double)As[li * n + c0] : (double)__ldg(A + i * a.lda + c0);
+      double y = li < ncache ? (double)As[QX(li * n + c0, a.rows_cached * n, 18)]
+                             : (double)__ldg(A + QX(i * a.lda + c0, m * a.lda, 19));
       for (int l = 0; l < j; ++l) y = fma(-vr[l], s_f[l], y);
-      vr[j] = y;
+      vr[QX(j, kp, 16)] = y;
       s2 = fma(y, y, s2);
       if constexpr (sizeof(AT) == 4) {
         const float h = (float)y;
         const float2 yp = make_float2(h, (float)(y - (double)h));
-        static_cast<float2 *>(ys)[li] = yp;
-        reinterpret_cast<float2 *>(a.Q)[i * a.ldq + j] = yp;  // V[i, j] as a pair, for the Q formation
+        static_cast<float2 *>(ys)[QX(li, a.rows_per, 20)] = yp;
+        reinterpret_cast<float2 *>(a.Q)[QX(i * a.ldq + j, m * a.ldq, 17)] = yp;  // V[i, j] as a pair, for the Q formation
       } else {
-        static_cast<double *>(ys)[li] = y;
+        static_cast<double *>(ys)[QX(li, a.rows_per, 20)] = y;
       }
     }
     PT *rp = reinterpret_cast<PT *>(red) + (size_t)par * L;
@@ -937,11 +960,11 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
         double u = 0.0;
         const int64_t lo = max((int64_t)0, (int64_t)j + 1 - r0);
         for (int64_t li = lo + (int64_t)aw * G + g; li < nrows; li += (int64_t)kAuxW * G) {
-          const double *vr = Vs + li * kp;
+          const double *vr = Vs + QX(li * kp, a.rows_per * kp, 21);
           if (l < j) u = fma(vr[l], vr[j], u);
         }
         for (int o = P; o < 32; o <<= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
-        if (g == 0) red4[kCT + aw * 32 + l] = u;  // [0, kCT) holds the ||y||^2 partials
+        if (g == 0) red4[QX(kCT + aw * 32 + l, 2 * kCT, 22)] = u;  // [0, kCT) holds the ||y||^2 partials
       }
       // ||y||^2: a tree over each thread's kCT / kAuxT partials, then over the lanes and warps
       double x[16];
@@ -955,8 +978,8 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
       if (at == 0) {
         double tt = red4[kCT + 64];
         for (int w2 = 1; w2 < kAuxW; ++w2) tt += red4[kCT + 64 + w2];
-        rp[n + k] = Part<PT>::of(tt);
-        rp[n + k + 1] = Part<PT>::of(owner ? Vs[(j - r0) * kp + j] : 0.0);
+        rp[QX(n + k, L, 23)] = Part<PT>::of(tt);
+        rp[QX(n + k + 1, L, 23)] = Part<PT>::of(owner ? Vs[QX((j - r0) * kp + j, a.rows_per * kp, 24)] : 0.0);
       }
       for (int q = at; q < k; q += kAuxT) {
         double tt = 0.0;
@@ -964,8 +987,8 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
           tt = red4[kCT + q];
           for (int w2 = 1; w2 < kAuxW; ++w2) tt += red4[kCT + w2 * 32 + q];
         }
-        rp[n + q] = Part<PT>::of(tt);
-        rp[n + k + 2 + q] = Part<PT>::of((owner && q < j) ? Vs[(j - r0) * kp + q] : 0.0);
+        rp[QX(n + q, L, 23)] = Part<PT>::of(tt);
+        rp[QX(n + k + 2 + q, L, 23)] = Part<PT>::of((owner && q < j) ? Vs[QX((j - r0) * kp + q, a.rows_per * kp, 24)] : 0.0);
       }
     }
     __syncthreads();
@@ -988,10 +1011,10 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
       s_sc[0] = v0;
       s_sc[1] = tau;
       s_sc[2] = v0 - x0;
-      Vt[j * k + j] = v0;
+      Vt[QX(j * k + j, k * k, 25)] = v0;
       if (owner) {
-        Vs[(j - r0) * kp + j] = v0;
-        if constexpr (sizeof(AT) == 4) reinterpret_cast<float2 *>(a.Q)[(int64_t)j * a.ldq + j] = df2_of(v0);
+        Vs[QX((j - r0) * kp + j, a.rows_per * kp, 24)] = v0;
+        if constexpr (sizeof(AT) == 4) reinterpret_cast<float2 *>(a.Q)[QX((int64_t)j * a.ldq + j, m * a.ldq, 17)] = df2_of(v0);
       }
       if (blockIdx.x == 0) {
         if (a.rdiag) a.rdiag[j] = beta;
@@ -1004,11 +1027,11 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
     if (colt) {
       int l = 0;
       for (; l + 1 < j; l += 2) {  // two independent chains each
-        const double f0 = Fo[(int64_t)l * no + lc], f1 = Fo[(int64_t)(l + 1) * no + lc];
+        const double f0 = Fo[QX((int64_t)l * no + lc, (int64_t)k * no, 26)], f1 = Fo[QX((int64_t)(l + 1) * no + lc, (int64_t)k * no, 26)];
         cs0 = fma(f0, svs[l], cs0);
         cs1 = fma(f1, svs[l + 1], cs1);
-        cv0 = fma(svs[k + 2 + l], f0, cv0);
-        cv1 = fma(svs[k + 2 + l + 1], f1, cv1);
+        cv0 = fma(svs[QX(k + 2 + l, 2 * k + 2, 27)], f0, cv0);
+        cv1 = fma(svs[QX(k + 2 + l + 1, 2 * k + 2, 27)], f1, cv1);
       }
       if (l < j) {
         const double f0 = Fo[(int64_t)l * no + lc];
@@ -1041,7 +1064,7 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
       const double rv = cv0 + cv1;             // F[c, :j] V[j, :j]^T
       const double corr = fma(v0, rv, cs0 + cs1);
       const double f = tau * (w - corr);
-      Fo[(int64_t)j * no + lc] = f;
+      Fo[QX((int64_t)j * no + lc, (int64_t)k * no, 26)] = f;
       double r = ajc - rv;
       r = fma(-v0, f, r);
       double nv = vno[lc] - r * r;
@@ -1061,18 +1084,19 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
       for (int q = tid; q < L; q += kCT) rq[q] = Part<PT>::zero();
       __syncthreads();
       for (unsigned q = 0; q < tm.S; ++q) {
-        const int *pf = cl.map_shared_rank(flago, q);
-        const double *pF = cl.map_shared_rank(Fo, q);
+        const int *pf = cl.map_shared_rank(flago, (unsigned)QX(q, tm.S, 28));
+        const double *pF = cl.map_shared_rank(Fo, (unsigned)QX(q, tm.S, 28));
         const int nq = (int)((n - (int64_t)q + tm.S - 1) / tm.S);
         for (int lc = 0; lc < nq; ++lc) {
-          if (!pf[lc]) continue;
+          if (!pf[QX(lc, no, 29)]) continue;
           const int64_t c = q + (int64_t)tm.S * lc;
-          if (tid <= j) s_f[tid] = pF[(int64_t)tid * no + lc];
+          if (tid <= j) s_f[QX(tid, 64, 11)] = pF[QX((int64_t)tid * no + lc, (int64_t)k * no, 30)];
           __syncthreads();
           double t = 0.0;
           for (int64_t li = max((int64_t)0, (int64_t)j + 1 - r0) + tid; li < nrows; li += kCT) {
-            double y = li < ncache ? (double)As[li * n + c] : (double)__ldg(A + (r0 + li) * a.lda + c);
-            const double *vr = Vs + li * kp;
+            double y = li < ncache ? (double)As[QX(li * n + c, a.rows_cached * n, 31)]
+                                   : (double)__ldg(A + QX((r0 + li) * a.lda + c, m * a.lda, 32));
+            const double *vr = Vs + QX(li * kp, a.rows_per * kp, 33);
             for (int l = 0; l <= j; ++l) y = fma(-vr[l], s_f[l], y);
             t = fma(y, y, t);
           }
@@ -1084,7 +1108,7 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
             for (int w = 0; w < kCW; ++w) u += red4[w * 32 + lane];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
-            if (lane == 0) rq[c] = Part<PT>::of(u);
+            if (lane == 0) rq[QX(c, L, 34)] = Part<PT>::of(u);
           }
           __syncthreads();
         }
@@ -1126,12 +1150,12 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int64_t idx = b0 + (int64_t)u * kCT;
-        if (idx < tot) v[u] = Qf[(r0 + idx / k) * a.ldq + idx % k];
+        if (idx < tot) v[u] = Qf[QX((r0 + idx / k) * a.ldq + idx % k, m * a.ldq, 35)];
       }
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int64_t idx = b0 + (int64_t)u * kCT;
-        if (idx < tot) Vsf[(idx / k) * kp + idx % k] = v[u];
+        if (idx < tot) Vsf[QX((idx / k) * kp + idx % k, a.rows_per * kp, 36)] = v[u];
       }
     }
     for (int q = tid; q < k * k; q += kCT) Mf[q] = df2_of(Ms[q]);  // each slot read, then rewritten, by one thread
@@ -1143,9 +1167,9 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
       t.hi = (i == cc) ? 1.f : 0.f;
       t.lo = 0.f;
       const int lmax = (int)min((int64_t)k - 1, i);
-      const float2 *vr = Vsf + li * kp;
+      const float2 *vr = Vsf + QX(li * kp, a.rows_per * kp, 37);
       for (int l = 0; l <= lmax; ++l) df_sub_prod(t, vr[l], Mf[l * k + cc]);
-      a.Q[i * a.ldq + cc] = f2d_exact(t.hi) + f2d_exact(t.lo);
+      a.Q[QX(i * a.ldq + cc, m * a.ldq, 38)] = f2d_exact(t.hi) + f2d_exact(t.lo);
     }
   } else {
     for (int64_t idx = tid; idx < nrows * k; idx += kCT) {
@@ -1153,11 +1177,12 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
       const int cc = (int)(idx % k);
       double t = (i == cc) ? 1.0 : 0.0;
       const int lmax = (int)min((int64_t)k - 1, i);
-      const double *vr = Vs + li * kp;
+      const double *vr = Vs + QX(li * kp, a.rows_per * kp, 37);
       for (int l = 0; l <= lmax; ++l) t = fma(-vr[l], Ms[l * k + cc], t);
-      a.Q[i * a.ldq + cc] = t;
+      a.Q[QX(i * a.ldq + cc, m * a.ldq, 38)] = t;
     }
   }
+  qc_report(a.err);
   cl.sync();  // no block leaves while a peer may still read its shared memory
 }
 
@@ -1221,6 +1246,19 @@ const char *qrp_form_env() {
 }
 
 }  // namespace
+
+// Checked build: the first site whose index fell outside its array (0: none), read after
+// synchronising the device; -1 in the normal build (no checks compiled in).
+int32_t qrp_check_site() {
+#ifdef TUCKER_QRP_CHECKED
+  unsigned site = 0;
+  if (cudaDeviceSynchronize() != cudaSuccess) return -2;
+  if (cudaMemcpyFromSymbol(&site, g_qc_site, sizeof(site)) != cudaSuccess) return -2;
+  return (int32_t)site;
+#else
+  return -1;
+#endif
+}
 
 // Runs the cluster form when its shared-memory plan fits; false = not applicable
 // (the caller runs another form).  *err reports a failed launch that was attempted.

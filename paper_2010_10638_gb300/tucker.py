@@ -21,7 +21,8 @@ import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libtucker.so")
+# TUCKER_LIB_PATH selects another build of the same library (the checked build of the tests)
+LIB_PATH = os.environ.get("TUCKER_LIB_PATH") or os.path.join(_HERE, "_build", "libtucker.so")
 
 TUCKER_F_BF16_FACTORS = 0x1
 TUCKER_F_QRP_DIRECT = 0x2
@@ -39,7 +40,7 @@ EXPORTS = ["tucker_init", "ttmc_mode", "ttmc_mode_norms", "qrp_leading", "qrp_le
            "tucker_phase_times", "tucker_kernel_launches", "qrp_leading_noalloc", "qrp_leading_noalloc_max_bytes",
            "tucker_selftest_wait", "tucker_mode_info", "qrp_leading_sync_status",
            "qrp_leading_noalloc_sync_status", "tucker_fp32_fma_tflops", "tucker_hooi_graph", "tucker_lib_setup",
-           "tucker_selftest_sort_wait"]
+           "tucker_selftest_sort_wait", "tucker_check_site"]
 
 
 class TuckerError(RuntimeError):
@@ -109,6 +110,8 @@ def load(path: str = LIB_PATH):
     lib.tucker_selftest_sort_wait.restype = cint
     lib.tucker_lib_setup.argtypes = [cint]
     lib.tucker_lib_setup.restype = cint
+    lib.tucker_check_site.argtypes = []
+    lib.tucker_check_site.restype = ctypes.c_int32
     lib.tucker_kernel_launches.argtypes = []
     lib.tucker_kernel_launches.restype = ctypes.c_uint64
     for name in ("tucker_init", "ttmc_mode", "qrp_leading", "hooi_iter", "core_tensor", "tucker_get_factor",
@@ -410,6 +413,12 @@ def tucker_fp32_fma_tflops(iters: int = 20000, stream=None) -> float:
 
 def tucker_kernel_launches() -> int:
     return int(load().tucker_kernel_launches())
+
+
+def tucker_check_site() -> int:
+    """Checked build: the first index check of the cluster QRP that failed (0: none); -1 in
+    the normal build."""
+    return int(load().tucker_check_site())
 
 
 def qrp_leading_noalloc_max_bytes() -> int:

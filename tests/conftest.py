@@ -14,6 +14,17 @@ def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a) and the built library")
 
 
+def pytest_sessionfinish(session, exitstatus):
+    """Under TUCKER_CHECK_REPORT (set by the checked-build test for its child run): write the
+    library's tucker_check_site() after all tests, from the process that ran the kernels."""
+    out = os.environ.get("TUCKER_CHECK_REPORT")
+    if not out:
+        return
+    from paper_2010_10638_gb300 import tucker
+    with open(out, "w") as f:
+        f.write(str(tucker.tucker_check_site()))
+
+
 @pytest.fixture(scope="session")
 def golden_dir():
     return GOLDEN
