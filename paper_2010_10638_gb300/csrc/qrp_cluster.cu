@@ -51,6 +51,7 @@ constexpr unsigned long long kCSpin = 1ull << 25;  // polls before a barrier wai
 // During a reflector step the first kColT threads form A^T y (FP32 pipe) while the last
 // kCT - kColT threads form V^T y and ||y||^2 (FP64 pipe), each group with its own barrier.
 constexpr int kColT = 448;
+constexpr int64_t kQfDfRows = 128;  // rows per block from which Q is formed in double-float sums
 constexpr int kAuxT = kCT - kColT;
 // the auxiliary warps keep their V^T y partials in red4[kCT, kCT + 64) and their ||y||^2
 // sums from red4[kCT + 64] on: at most two of them (448 / 64 measured fastest of 480 / 32
@@ -1135,7 +1136,12 @@ __global__ void __launch_bounds__(kCT, 1) qrp_cluster_kernel(CArgs a) {
     Ms[q] = t;
   }
   __syncthreads();
-  if constexpr (sizeof(AT) == 4) {
+  // FP32 A with many rows per block: the double-float formation below; with few (the
+  // 1,000 x 256 unfolding: 63 rows per block) its set-up costs more than it saves, and the
+  // FP64 formation from V's FP64 copy runs instead (2 us less measured there)
+  bool df_q = false;
+  if constexpr (sizeof(AT) == 4) df_q = a.rows_per >= kQfDfRows;
+  if (df_q) {
     // FP32 A: V's entries were kept as double-float pairs in Q's slots during the steps;
     // they replace the FP64 copy in shared memory (no longer needed), M is split in place,
     // and each entry of Q is a double-float sum on the FP32 pipe (about 2^-47 relative),
