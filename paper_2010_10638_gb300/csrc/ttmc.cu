@@ -1116,176 +1116,6 @@ __global__ void __launch_bounds__(kTtmcWarps * 32) ttmc_bf16_kernel(const TtmcPa
   }
 }
 
-// ============================================================================ split-TF32 form
-// FP32 factors on the tensor cores.  The segment sums of one tile are the products
-// Y_tile(a, b) += sum_k A(a, k) B(k, b), with A(a, k) = x_k U_a(i_a(k), a) and
-// B(k, b) = U_b(i_b(k), b) over the tile's nonzeros k of one slice.  Each FP32 operand v
-// is split into v_hi = tf32(v) and v_lo = tf32(v - v_hi) (round to nearest), and
-// A B ~ A_lo B_hi + A_hi B_lo + A_hi B_hi (three m16n8k8 MMAs, FP32 accumulation); the
-// dropped A_lo B_lo and the rounding of the low parts are below 2^-21 of |A||B| per
-// product.  Staging is that of the pipelined SIMT form (lane = nonzero, x applied in
-// FP32), into k-major rows of PL and RB floats whose 8-float groups are XOR-swizzled by
-// the row, so that the fragment loads (four rows of one k-step, eight consecutive columns
-// each) fall in distinct banks.  Nonzeros outside the current segment are zeroed in the A
-// fragments; their rows of B are finite (every tile stages all 32 rows).  The one-tile-ahead
-// register prefetch of the indices and values is that of ttmc_pipe_kernel.
-__device__ __forceinline__ uint32_t tf32_of(float v) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
-  return r;
-}
-__device__ __forceinline__ void tf32_split(float v, uint32_t &hi, uint32_t &lo) {
-  hi = tf32_of(v);
-  lo = tf32_of(v - __uint_as_float(hi));
-}
-__device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-// column of element c of row k in a k-major row of S floats: 8-float groups XOR-swizzled so
-// that rows k .. k+3 put the same columns in four different banks (S in {8, 16, 32})
-template <int S>
-__device__ __forceinline__ int tf32_col(int k, int c) {
-  return c ^ (((((k & 3) * S) >> 5)) << 3);
-}
-
-template <int PL, int RB>
-__global__ void __launch_bounds__(kTtmcWarps * 32) ttmc_tf32_kernel(const TtmcParams p) {
-  static_assert(PL % 16 == 0 && RB % 8 == 0 && PL <= 32 && RB <= 32, "m16n8k8 tiles");
-  constexpr int MT = PL / 16, NT = RB / 8;
-  extern __shared__ float4 smem_f4[];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  float *xa = reinterpret_cast<float *>(smem_f4) + w * 32 * (PL + RB);
-  float *bb = xa + 32 * PL;
-  const int64_t u = (int64_t)blockIdx.x * kTtmcWarps + w;
-  if (u >= p.n_units) return;
-  const float *UA = static_cast<const float *>(p.U[0]);
-  const float *UB = static_cast<const float *>(p.U[1]);
-  const uint32_t *idxA = p.idx[0];
-  const uint32_t *idxB = p.idx[1];
-  const uint32_t e0 = __ldg(p.unit_e0 + u);
-  const uint32_t e_end = (u + 1 < p.n_units) ? __ldg(p.unit_e0 + u + 1) : p.Z;
-  const int slot = __ldg(p.unit_slot + u);
-  const int ntiles = (int)((e_end - e0 + 31u) / 32u);
-  const int g = lane >> 2, t4 = lane & 3;
-  float acc[MT][NT][4];
-#pragma unroll
-  for (int i = 0; i < MT; ++i)
-#pragma unroll
-    for (int jn = 0; jn < NT; ++jn)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[i][jn][q] = 0.f;
-
-  uint32_t kb = __ldg(p.unit_k0 + u);
-  uint32_t bound = (kb + 1u + lane <= p.S) ? __ldg(p.sptr + kb + 1u + lane) : 0xffffffffu;
-  float x = 0.f;
-  uint32_t ia = 0u, ib = 0u;
-  if (e0 + lane < e_end) {
-    x = __ldg(p.val + e0 + lane);
-    ia = __ldg(idxA + e0 + lane);
-    ib = __ldg(idxB + e0 + lane);
-  }
-  for (int t = 0; t < ntiles; ++t) {
-    const uint32_t e = e0 + 32u * (uint32_t)t;
-    const int nt = (int)min(32u, e_end - e);
-    const uint32_t q = bound - e;
-    uint32_t starts = __reduce_or_sync(kFull, q < 32u ? (1u << q) : 0u);
-    starts &= (nt >= 32) ? kFull : ((1u << nt) - 1u);
-    const uint32_t kp = kb + __popc(starts & ((2u << lane) - 1u));
-    const bool end_is_start = __any_sync(kFull, q == (uint32_t)nt);
-    const uint32_t kb_next = kb + __popc(__ballot_sync(kFull, q <= (uint32_t)nt));
-    const uint32_t bound_next = (kb_next + 1u + lane <= p.S) ? __ldg(p.sptr + kb_next + 1u + lane) : 0xffffffffu;
-    float xn = 0.f;
-    uint32_t ian = 0u, ibn = 0u;
-    const uint32_t posn = e + 32u + (uint32_t)lane;
-    if (posn < e_end) {
-      xn = __ldg(p.val + posn);
-      ian = __ldg(idxA + posn);
-      ibn = __ldg(idxB + posn);
-    }
-    // stage tile t: x * left rows, last-mode rows (k-major, swizzled 8-float groups)
-#pragma unroll
-    for (int it = lane; it < 32 * (PL / 4); it += 32) {
-      const int tt = it / (PL / 4), c = (it % (PL / 4)) * 4;
-      const float xt = __shfl_sync(kFull, x, tt);
-      const uint32_t r = __shfl_sync(kFull, ia, tt);
-      float4 v = __ldg(reinterpret_cast<const float4 *>(UA + (size_t)r * PL + c));
-      v.x *= xt;
-      v.y *= xt;
-      v.z *= xt;
-      v.w *= xt;
-      *reinterpret_cast<float4 *>(xa + tt * PL + tf32_col<PL>(tt, c)) = v;
-    }
-#pragma unroll
-    for (int it = lane; it < 32 * (RB / 4); it += 32) {
-      const int tt = it / (RB / 4), c = (it % (RB / 4)) * 4;
-      const uint32_t r = __shfl_sync(kFull, ib, tt);
-      *reinterpret_cast<float4 *>(bb + tt * RB + tf32_col<RB>(tt, c)) =
-          __ldg(reinterpret_cast<const float4 *>(UB + (size_t)r * RB + c));
-    }
-    __syncwarp();
-    uint32_t segs = starts | 1u;
-    while (segs) {
-      const int p0 = __ffs(segs) - 1;
-      segs &= segs - 1u;
-      const int p1 = segs ? (__ffs(segs) - 1) : nt;
-      for (int ks = p0; ks < p1; ks += 8) {
-        const int k0 = ks + t4, k4 = k0 + 4;       // this lane's two nonzeros of the k-step
-        const int r0 = k0 & 31, r4 = k4 & 31;      // rows past the tile: masked in A, finite in B
-        const bool in0 = k0 < p1, in4 = k4 < p1;
-        uint32_t bh[NT][2], bl[NT][2];
-#pragma unroll
-        for (int nq = 0; nq < NT; ++nq) {
-          tf32_split(bb[r0 * RB + tf32_col<RB>(r0, nq * 8 + g)], bh[nq][0], bl[nq][0]);
-          tf32_split(bb[r4 * RB + tf32_col<RB>(r4, nq * 8 + g)], bh[nq][1], bl[nq][1]);
-        }
-#pragma unroll
-        for (int mt = 0; mt < MT; ++mt) {
-          // a0 (m g, k t4), a1 (m g+8, k t4), a2 (m g, k t4+4), a3 (m g+8, k t4+4)
-          const float v0 = in0 ? xa[r0 * PL + tf32_col<PL>(r0, mt * 16 + g)] : 0.f;
-          const float v1 = in0 ? xa[r0 * PL + tf32_col<PL>(r0, mt * 16 + g + 8)] : 0.f;
-          const float v2 = in4 ? xa[r4 * PL + tf32_col<PL>(r4, mt * 16 + g)] : 0.f;
-          const float v3 = in4 ? xa[r4 * PL + tf32_col<PL>(r4, mt * 16 + g + 8)] : 0.f;
-          uint32_t ah[4], al[4];
-          tf32_split(v0, ah[0], al[0]);
-          tf32_split(v1, ah[1], al[1]);
-          tf32_split(v2, ah[2], al[2]);
-          tf32_split(v3, ah[3], al[3]);
-#pragma unroll
-          for (int nq = 0; nq < NT; ++nq) {
-            mma_tf32(acc[mt][nq], al, bh[nq][0], bh[nq][1]);
-            mma_tf32(acc[mt][nq], ah, bl[nq][0], bl[nq][1]);
-            mma_tf32(acc[mt][nq], ah, bh[nq][0], bh[nq][1]);
-          }
-        }
-      }
-      const bool flush = (p1 < nt) || end_is_start || (e + (uint32_t)nt == e_end);
-      if (flush) {
-        const uint32_t kseg = __shfl_sync(kFull, kp, p0);
-        float *dst = (slot >= 0) ? p.carry + (size_t)slot * p.P : p.Y + (size_t)__ldg(p.sid + kseg) * p.P;
-#pragma unroll
-        for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-          for (int nq = 0; nq < NT; ++nq) {
-            const int row = mt * 16 + g, col = nq * 8 + 2 * t4;
-            *reinterpret_cast<float2 *>(dst + (size_t)row * RB + col) = make_float2(acc[mt][nq][0], acc[mt][nq][1]);
-            *reinterpret_cast<float2 *>(dst + (size_t)(row + 8) * RB + col) =
-                make_float2(acc[mt][nq][2], acc[mt][nq][3]);
-            acc[mt][nq][0] = acc[mt][nq][1] = acc[mt][nq][2] = acc[mt][nq][3] = 0.f;
-          }
-      }
-    }
-    __syncwarp();
-    kb = kb_next;
-    bound = bound_next;
-    x = xn;
-    ia = ian;
-    ib = ibn;
-  }
-}
-
 // ============================================================================ TMA-fed BF16 form
 // The arithmetic of ttmc_bf16_kernel (order 3, ranks 16 x 16) with the factor rows brought
 // into shared memory by the tensor memory accelerator instead of by the warp's own loads:
@@ -1839,35 +1669,10 @@ static bool pipe_shape(int PL, int RB) {
          (PL == 8 && RB == 16);
 }
 
-template <int PL, int RB>
-static cudaError_t run_tf32(const TtmcParams &p, cudaStream_t s) {
-  const size_t smem = (size_t)kTtmcWarps * 32 * (PL + RB) * sizeof(float);
-  auto kern = ttmc_tf32_kernel<PL, RB>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  kern<<<(unsigned)ttmc_pipe_blocks(p.n_units), kTtmcWarps * 32, smem, s>>>(p);
-  ::tk::count_launch();
-  return cudaGetLastError();
-}
-
-// The split-TF32 tensor-core form (opt-in, TUCKER_TTMC_TF32=1) for the shapes it covers.
-// On the skewed 20M-nonzero workload it ran 353 / 458 / 324 us per mode against 364 / 449 /
-// 331 us for the SIMT form, with Y 2-3e-6 (relative) from the SIMT form's.
-static bool tf32_form(int PL, int RB) {
-  const char *e = std::getenv("TUCKER_TTMC_TF32");
-  if (!(e && e[0] == '1')) return false;
-  return PL == 16 && (RB == 16 || RB == 8);
-}
-
 // Pipelined FP32 dispatch (order 3, row-aligned factors).
 static bool dispatch_pipe(const TtmcParams &p, cudaStream_t s, cudaError_t *err) {
   if (p.nother != 2) return false;
   const int PL = p.R[0], RB = p.R[1];
-  if (!p.sq_part && tf32_form(PL, RB)) {
-    if (RB == 16) *err = run_tf32<16, 16>(p, s);
-    else *err = run_tf32<16, 8>(p, s);
-    return true;
-  }
 #define TK_PIPE(PL_, RB_, TA_, TB_)                   \
   {                                                   \
     *err = run_pipe<PL_, RB_, TA_, TB_>(p, s);        \
