@@ -14,7 +14,7 @@ above the FP32 rounding of Y_(n) (smallest 7.6e-6 relative), so the same pivots 
 chosen and the factors compared column by column.
 
 BF16 factors (order4-5M, skew-20M): the fit after every sweep within 1e-2 of the FP64
-oracle's (the benchmark spec's BF16 bar, taken on the fit); the observed error is printed."""
+oracle's (the BF16 form's stated 1e-2 bar, taken on the fit); the observed error is printed."""
 import json
 import os
 
