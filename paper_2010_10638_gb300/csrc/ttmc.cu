@@ -504,7 +504,9 @@ __global__ void __launch_bounds__(kTtmcWarps * 32, 4) ttmc_pipe_sq_kernel(const 
 // depend on slices).  One fiber per group of QL = RB/4 lanes (lane q of the group owns the
 // column quad t_f[4q, 4q+4)), 32/QL fibers of the warp side by side; a group adds its
 // fiber's positions in order (fibers are at most kFiberCap long), with the values, indices
-// and factor rows of four positions in flight at a time.  One fixed order: t is reproducible.
+// and factor rows of four positions in flight at a time; with four or more lanes per fiber
+// the values and indices of the four positions are loaded once (one position per lane) and
+// shared by shuffles within the group.  One fixed order: t is reproducible.
 template <int RB>
 __global__ void __launch_bounds__(kTtmcWarps * 32) ttmc_fibsum_kernel(const TtmcParams p, float *__restrict__ T,
                                                                      int64_t fpw) {
@@ -528,11 +530,29 @@ __global__ void __launch_bounds__(kTtmcWarps * 32) ttmc_fibsum_kernel(const Ttmc
     for (uint32_t z = zs; z < ze; z += 4u) {
       float xv[4];
       uint32_t iv[4];
+      if constexpr (QL >= 4) {
+        // lane q < 4 of the group loads position z + q; the group's lanes (all on this
+        // fiber, so all in this loop) take the four values and indices by shuffle
+        const unsigned gmask = ((QL == 32) ? 0xffffffffu : ((1u << QL) - 1u)) << (g * QL);
+        const uint32_t zq = z + (uint32_t)q;
+        float xm = 0.f;
+        uint32_t im = 0u;
+        if (q < 4 && zq < ze) {
+          xm = __ldg(p.val + zq);
+          im = __ldg(idxB + zq);
+        }
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const bool in = z + (uint32_t)k < ze;
-        xv[k] = in ? __ldg(p.val + z + k) : 0.f;
-        iv[k] = in ? __ldg(idxB + z + k) : 0u;
+        for (int k = 0; k < 4; ++k) {
+          xv[k] = __shfl_sync(gmask, xm, k, QL);
+          iv[k] = __shfl_sync(gmask, im, k, QL);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const bool in = z + (uint32_t)k < ze;
+          xv[k] = in ? __ldg(p.val + z + k) : 0.f;
+          iv[k] = in ? __ldg(idxB + z + k) : 0u;
+        }
       }
       float4 r[4];
 #pragma unroll
