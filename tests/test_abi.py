@@ -43,6 +43,22 @@ def test_status_strings_without_a_gpu():
     assert lib.tucker_status_str(2) == b"rank out of range"
 
 
+def test_normal_build_has_no_index_checks():
+    """tucker_check_site is -1 in the normal build (no checks compiled in, no CUDA call)."""
+    from paper_2010_10638_gb300 import build
+    lib = ctypes.CDLL(build.build())
+    lib.tucker_check_site.restype = ctypes.c_int32
+    assert lib.tucker_check_site() == -1
+
+
+def test_ttmc_norms_flag_is_declared():
+    with open(os.path.join(ROOT, "include", "tucker.h")) as f:
+        text = f.read()
+    from paper_2010_10638_gb300 import tucker
+    m = re.search(r"#define\s+TUCKER_F_TTMC_NORMS\s+(0x[0-9a-fA-F]+)u", text)
+    assert m and int(m.group(1), 16) == tucker.TUCKER_F_TTMC_NORMS
+
+
 def test_device_entry_points_refuse_host_tensors():
     """No host fallback: the device entry points reject CPU tensors and other dtypes
     before any call into the library."""
