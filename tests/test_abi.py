@@ -51,12 +51,18 @@ def test_normal_build_has_no_index_checks():
     assert lib.tucker_check_site() == -1
 
 
-def test_ttmc_norms_flag_is_declared():
+def test_binding_flags_match_the_header():
+    """Every TUCKER_F_* flag of the header has the same value in the binding, and no two
+    flags share a bit."""
     with open(os.path.join(ROOT, "include", "tucker.h")) as f:
         text = f.read()
     from paper_2010_10638_gb300 import tucker
-    m = re.search(r"#define\s+TUCKER_F_TTMC_NORMS\s+(0x[0-9a-fA-F]+)u", text)
-    assert m and int(m.group(1), 16) == tucker.TUCKER_F_TTMC_NORMS
+    flags = {k: int(v, 16) for k, v in re.findall(r"#define\s+(TUCKER_F_\w+)\s+(0x[0-9a-fA-F]+)u", text)}
+    assert "TUCKER_F_TTMC_NORMS" in flags and len(flags) >= 6
+    for name, value in flags.items():
+        assert getattr(tucker, name) == value, name
+    bits = list(flags.values())
+    assert all(b & (b - 1) == 0 for b in bits) and len(set(bits)) == len(bits)
 
 
 def test_device_entry_points_refuse_host_tensors():
